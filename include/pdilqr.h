@@ -1,0 +1,235 @@
+/*
+ * pdilqr.h -- C ABI of the B300 primal-dual iLQR hot path.
+ *
+ * The library solves the linear-quadratic KKT system of each primal-dual
+ * iLQR (SQP) step by the parallel associative scan of Sec. II-D of
+ * "Primal-Dual iLQR for GPU-Accelerated Learning and Control in Legged
+ * Robots", together with the linearisation (Sec. II-B, II-F), the FP64
+ * residual and one refinement step, the parallel filter line search
+ * (Sec. II-E) and the SQP loop around them.
+ *
+ * Conventions (Sec. II-A/II-B, with N counting control intervals and the
+ * terminal cost on x_N):
+ *   states x_0..x_N in R^n, controls u_0..u_{N-1} in R^m,
+ *   costates lam_0..lam_N in R^n.
+ * A batch holds `count` instances with a common (n, m) and horizons N_i.
+ * Every per-stage array is packed instance after instance, N_i + 1 stage
+ * slots per instance starting at slot stage_off[i], row-major inside a stage:
+ *   A [n][n], B [n][m], c [n]      (dynamics, defect; slot N_i unused)
+ *   Q [n][n], q [n]                (slot N_i holds the terminal Q_N, q_N)
+ *   R [m][m], S [m][n], r [m]      (slot N_i unused; S may be NULL = 0)
+ *   dx [n], du [m] (slot N_i written 0), dlam [n], K [m][n], k [m], P [n][n], p [n]
+ * Unless stated otherwise every array argument is a DEVICE pointer owned by
+ * the caller (for instance allocated by PyTorch) and 16-byte aligned; the
+ * library never frees it.  All calls are asynchronous on the stream passed
+ * (NULL = legacy default stream) and return before the GPU work ends.
+ * Two calls that share a plan must not overlap on the GPU: the plan's
+ * workspace is shared.  Nothing throws across this boundary; every entry
+ * point returns a pdilqr_status and writes per-instance status words
+ * (int32, same codes) to device memory.
+ */
+#ifndef PDILQR_H
+#define PDILQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PDILQR_API __attribute__((visibility("default")))
+#else
+#define PDILQR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pdilqr_stream; /* == cudaStream_t */
+
+typedef enum {
+    PDILQR_OK = 0,
+    PDILQR_E_INVALID_ARG = 1,  /* bad size, null pointer, unsupported (n, m)      */
+    PDILQR_E_NOT_SPD = 2,      /* a Cholesky pivot of R_k or G_k was not positive */
+    PDILQR_E_SINGULAR = 3,     /* a pivot of (I + C P) vanished in a combine      */
+    PDILQR_E_NONFINITE = 4,    /* NaN / Inf met                                    */
+    PDILQR_E_TIMEOUT = 5,      /* a bounded device or host wait ran out            */
+    PDILQR_E_NO_MEMORY = 6,    /* device or pinned allocation failed               */
+    PDILQR_E_ADMISSION = 7,    /* the server refused a request (memory budget)     */
+    PDILQR_E_LINESEARCH = 8,   /* no step size of the grid was accepted            */
+    PDILQR_E_CUDA = 9          /* a CUDA runtime call failed                       */
+} pdilqr_status;
+
+/* Static string for a status code. */
+PDILQR_API const char *pdilqr_status_string(int status);
+
+/* ------------------------------------------------------------- batches */
+
+/* Host-side description of a batch (copied by pdilqr_plan_create). */
+typedef struct {
+    int32_t n;                 /* state dimension  (same for every instance)   */
+    int32_t m;                 /* control dimension                             */
+    int32_t count;             /* number of instances, >= 1                     */
+    const int32_t *N;          /* HOST [count] horizons, 1 <= N_i <= 4096       */
+    const int64_t *stage_off;  /* HOST [count] first stage slot of instance i;  */
+                               /* slots [off_i, off_i + N_i] must not overlap   */
+} pdilqr_batch;
+
+typedef struct {
+    int32_t warps;      /* warps per instance for the scan: 4, 8 or 16;      */
+                        /* 0 picks by the longest horizon of the batch      */
+    int32_t refine;     /* 0: plain FP32 solve; 1: one refinement step      */
+                        /* against the FP64-evaluated KKT residual          */
+} pdilqr_opts;
+
+typedef struct pdilqr_plan pdilqr_plan;
+
+/* Validate a batch, copy its description to the current CUDA device and
+ * allocate the plan's workspace (device memory, about (2n^2 + nm + 3n + m)
+ * floats per stage slot).  Supported (n, m): (1,1) (2,1) (3,2) (4,2) (12,12)
+ * and, for the Riccati comparator only, (36,24).  Errors: INVALID_ARG,
+ * NO_MEMORY, CUDA.  *out is NULL on error. */
+PDILQR_API pdilqr_status pdilqr_plan_create(const pdilqr_batch *batch, const pdilqr_opts *opts,
+                                 pdilqr_plan **out);
+PDILQR_API pdilqr_status pdilqr_plan_destroy(pdilqr_plan *plan);
+/* Warps per instance the plan uses for the scan (after the 0 -> pick rule). */
+PDILQR_API int32_t pdilqr_plan_warps(const pdilqr_plan *plan);
+
+/* ------------------------------------------------------- LQ KKT solves */
+
+/* LQ data of a batch (device, layout above).  In Sec. II-B notation: A, B the
+ * dynamics Jacobians, c the defects b_i, Q, R, S the Hessian blocks, q, r the
+ * Lagrangian gradients; slot N_i of Q, q is the terminal P_{N+1}, p_{N+1}. */
+typedef struct {
+    const float *A, *B, *c, *Q, *R, *S, *q, *r;
+} pdilqr_lq;
+
+typedef struct {
+    float *dx, *du, *dlam;     /* required outputs (search direction, Eq. QP)   */
+    float *K, *k, *P, *p;      /* optional outputs (NULL: kept in the plan)     */
+    int32_t *status;           /* required [count] per-instance status          */
+    double *resid;             /* optional [count][4]: infinity norms of the    */
+                               /* final KKT residual, of the KKT matrix (max    */
+                               /* absolute row sum), of z and of the right-hand */
+                               /* side; backward error = r0 / (r1 r2 + r3)      */
+} pdilqr_kkt_out;
+
+/* LQ KKT solve by the parallel associative scan (Sec. II-D): conditional
+ * value function elements (Eq. initialization) combined by the combination
+ * rule (corrected as documented in kkt_scan.cuh) in a chunked reduce-then-scan
+ * over the horizon, parallel policy recovery (Eq. lqr), the trajectory scan
+ * of Eq. (controlled_dynamics) and dlam_i = P_i dx_i + p_i.  s [count][n] is
+ * dx_0 = xhat_0 - x_0.  With opts.refine the KKT residual is evaluated in FP64
+ * and one correction solve is added.  One CTA per instance. */
+PDILQR_API pdilqr_status pdilqr_kkt_scan_solve(pdilqr_plan *plan, const pdilqr_lq *lq, const float *s,
+                                    pdilqr_kkt_out *out, pdilqr_stream stream);
+
+/* The same system by the sequential Riccati recursion and forward rollout of
+ * Sec. II-C (the comparator), one warp per instance; honours opts.refine. */
+PDILQR_API pdilqr_status pdilqr_riccati_solve(pdilqr_plan *plan, const pdilqr_lq *lq, const float *s,
+                                   pdilqr_kkt_out *out, pdilqr_stream stream);
+
+/* FP64 evaluation of the KKT residual of z = (dx, du, dlam); writes the four
+ * norms described under pdilqr_kkt_out.resid to resid [count][4] (device). */
+PDILQR_API pdilqr_status pdilqr_kkt_residual(pdilqr_plan *plan, const pdilqr_lq *lq, const float *s,
+                                  const float *dx, const float *du, const float *dlam,
+                                  double *resid, pdilqr_stream stream);
+
+/* ------------------------------------------------------ SRBD model, Sec. III */
+
+/* Single-rigid-body quadruped (the paper prints no equations; this is the
+ * library's reading).  Per robot x = [p, theta, v, omega] (n = 12) and
+ * u = [f_0..f_3] ground reaction forces (m = 12); with stance flags s_j:
+ *   p' = v,  theta' = omega,  v' = sum_j s_j f_j / mass - g e_z,
+ *   omega' = I^-1 ( sum_j s_j (foot_j - p) x f_j - omega x (I omega) ),
+ * one explicit Euler step of length dt.  Stage cost (Sec. II-F):
+ *   0.5 |x - xref|_W^2 + 0.5 |u - uref|_Wu^2 + sum over stance feet of the
+ *   relaxed barrier B(xi; bar_mu, bar_delta) of the five friction-pyramid rows
+ *   xi = mu f_z +- f_x, mu f_z +- f_y, f_z;
+ * terminal cost 0.5 |x_N - xref_N|_WN^2.  With nrob > 1 robots are stacked
+ * (n = m = 12 nrob) and a ring formation cost
+ * 0.5 w_form sum_a |p_a - p_{a+1 mod nrob} - d_form[a]|^2 is added at every
+ * stage.  The Hessian is the Gauss-Newton one of Sec. II-F. */
+typedef struct {
+    int32_t nrob;              /* robots stacked in one state (1 supported by   */
+                               /* the fused solver, up to 16 by linearize)      */
+    float w_form;              /* formation weight                              */
+    float d_form[16][3];       /* formation offsets                             */
+    float mass, inertia[3], dt, gravity;
+    float foot[4][3];          /* stance points, world frame                    */
+    float mu_fric, bar_mu, bar_delta;
+    float W[12], Wu[12], WN[12];   /* diagonal weights of one robot             */
+} pdilqr_srbd_model;
+
+/* Trajectory of a batch (device, N_i + 1 slots per instance):
+ * x, lam [n], u [m] (slot N_i unused), xref [n], uref [m],
+ * contact [nrob][4] uint8 stance flags, x0hat [count][n]. */
+typedef struct {
+    const float *x, *u, *lam, *xref, *uref;
+    const uint8_t *contact;
+} pdilqr_traj;
+
+/* Mutable LQ data (outputs of pdilqr_linearize), same layout as pdilqr_lq. */
+typedef struct {
+    float *A, *B, *c, *Q, *R, *S, *q, *r;
+} pdilqr_lq_out;
+
+/* Linearisation of Sec. II-B/II-F for every stage in parallel: A = dh/dx,
+ * B = dh/du, c_k = h(x_k, u_k) - x_{k+1}, Gauss-Newton Q, R (barrier
+ * curvature included), S = 0 (written if non-NULL), q = grad_x l + A^T
+ * lam_{k+1} - lam_k, r = grad_u l + B^T lam_{k+1}; slot N: Q_N, q_N =
+ * grad l_N - lam_N.  One warp per stage slot.  Needs n = m = 12 nrob. */
+PDILQR_API pdilqr_status pdilqr_linearize(pdilqr_plan *plan, const pdilqr_srbd_model *model,
+                                          const pdilqr_traj *traj, pdilqr_lq_out *out,
+                                          pdilqr_stream stream);
+
+/* Line-search merit of Sec. II-E for the ten step sizes alpha_t = 2^-t,
+ * t = 0..9, per instance: merit[count][24] (device, double) receives
+ *   [0] J(0)   [1] theta(0)   [2] dphi = grad J^T dz
+ *   [3 + t]  J(alpha_t) - J(0)   [13 + t] theta(alpha_t)   [23] unused,
+ * where theta = |xhat_0 - x_0|_2 + sum_k |x_{k+1} - h(x_k, u_k)|_2 and the
+ * cost differences are evaluated stage by stage in a cancellation-free form.
+ * dz = (dx, du) is the search direction (device, trajectory layout). */
+PDILQR_API pdilqr_status pdilqr_merit_eval(pdilqr_plan *plan, const pdilqr_srbd_model *model,
+                                           const pdilqr_traj *traj, const float *x0hat,
+                                           const float *dx, const float *du, double *merit,
+                                           pdilqr_stream stream);
+
+/* SQP options (Sec. II-E).  theta_max = theta_frac * max(1, theta(initial
+ * iterate)); above it a step must lower theta; below it a descent direction
+ * must satisfy Armijo J(a) <= J(0) + c_armijo a dphi with theta(a) <= theta_max,
+ * otherwise the cost or theta must drop.  The largest accepted step of the
+ * grid 2^0..2^-9 is taken. */
+typedef struct {
+    int32_t max_iters;         /* SQP iterations, 1..32                          */
+    float tol_step;            /* stop when |dz|_inf < tol_step and             */
+    float tol_theta;           /*   theta < tol_theta (0 never stops early)     */
+    float c_armijo;            /* Armijo constant (1e-4)                         */
+    float theta_frac;          /* theta_max fraction (1e-2)                      */
+    const float *alpha_replay; /* device [count][max_iters] step sizes to use    */
+                               /* instead of the line search, or NULL           */
+} pdilqr_sqp_opts;
+
+typedef struct {
+    int32_t *iters;            /* [count] KKT solves performed                   */
+    int32_t *status;           /* [count] OK, LINESEARCH, NOT_SPD, SINGULAR      */
+    float *alpha;              /* [count][max_iters] steps taken (optional)      */
+    double *J, *theta;         /* [count] merit at the returned iterate (opt.)   */
+} pdilqr_sqp_info;
+
+/* Full multiple-shooting SQP (Sec. II-B..II-E) on the SRBD model: per
+ * iteration the linearisation, the LQ KKT solve by the parallel scan, the
+ * parallel line search over the ten step sizes and the update
+ * x += a dx, u += a du, lam += a dlam (Eq. linear_rollout), all in one
+ * kernel with one CTA per instance and no host synchronisation.  x, u, lam
+ * (device, trajectory layout) hold the warm start on entry and the solution
+ * on exit.  Needs n = m = 12 (nrob = 1). */
+PDILQR_API pdilqr_status pdilqr_solve(pdilqr_plan *plan, const pdilqr_srbd_model *model,
+                                      const pdilqr_sqp_opts *opts, const float *x0hat,
+                                      float *x, float *u, float *lam, const float *xref,
+                                      const float *uref, const uint8_t *contact,
+                                      pdilqr_sqp_info *info, pdilqr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDILQR_H */

@@ -1,0 +1,255 @@
+// dev_linalg.cuh -- small dense linear algebra for one thread group.
+//
+// A "group" is NT threads (one warp, or several warps joined by a named
+// barrier) that cooperates on one matrix operation.  Operands live in shared
+// memory (or global memory for read-only operands), row-major with an
+// explicit leading dimension; every size is a compile-time constant so the
+// loops unroll.  Each operation ends with a group barrier unless told not to,
+// so its result may be read by any thread of the group afterwards.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace pdl {
+
+__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ constexpr int round4(int a) { return (a + 3) & ~3; }
+
+template <int NT>
+struct Grp {
+    int t;    // rank inside the group
+    int bar;  // named barrier id (groups wider than one warp)
+    __device__ __forceinline__ void sync() const {
+        if constexpr (NT == 32) {
+            __syncwarp();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(NT) : "memory");
+        }
+    }
+};
+
+// Register tile (RT x CT) for an R x C result spread over NT threads: the
+// smallest tile whose tile count fits in NT, ties broken by fewer operand
+// loads (RT + CT); tiles are capped at 4 x 4 (larger results loop).
+template <int R, int C, int NT>
+struct TilePick {
+    __host__ __device__ static constexpr int pick() {
+        for (int area = 1; area <= 16; ++area) {
+            int best = -1, best_cost = 1 << 30;
+            for (int rt = 1; rt <= 4; ++rt) {
+                if (area % rt) continue;
+                int ct = area / rt;
+                if (ct > 4) continue;
+                if (cdiv(R, rt) * cdiv(C, ct) > NT) continue;
+                if (rt + ct < best_cost) { best_cost = rt + ct; best = rt * 8 + ct; }
+            }
+            if (best >= 0) return best;
+        }
+        return 4 * 8 + 4;
+    }
+    static constexpr int RT = pick() / 8;
+    static constexpr int CT = pick() % 8;
+};
+
+// out[R][C] = D + sgn * op(A) op(B)   (D == nullptr: no addend)
+// op(A)(r,l) = TA ? A[l*lda + r] : A[r*lda + l];  op(B)(l,c) likewise.
+// out must not alias A or B; it may alias D.
+template <int R, int C, int K, bool TA, bool TB, int NT, bool SYNC = true>
+__device__ __forceinline__ void mm(const Grp<NT>& g, float* out, int ldo,
+                                   const float* A, int lda, const float* B, int ldb,
+                                   const float* D = nullptr, int ldd = 0, float sgn = 1.f)
+{
+    constexpr int RT = TilePick<R, C, NT>::RT, CT = TilePick<R, C, NT>::CT;
+    constexpr int TR = cdiv(R, RT), TC = cdiv(C, CT), NTILE = TR * TC;
+    for (int tile = g.t; tile < NTILE; tile += NT) {
+        const int r0 = (tile / TC) * RT, c0 = (tile % TC) * CT;
+        float acc[RT][CT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int j = 0; j < CT; ++j) acc[i][j] = 0.f;
+#pragma unroll(K <= 24 ? K : 8)
+        for (int l = 0; l < K; ++l) {
+            float a[RT], b[CT];
+#pragma unroll
+            for (int i = 0; i < RT; ++i) {
+                const int r = (R % RT == 0) ? r0 + i : min(r0 + i, R - 1);
+                a[i] = TA ? A[l * lda + r] : A[r * lda + l];
+            }
+#pragma unroll
+            for (int j = 0; j < CT; ++j) {
+                const int c = (C % CT == 0) ? c0 + j : min(c0 + j, C - 1);
+                b[j] = TB ? B[c * ldb + l] : B[l * ldb + c];
+            }
+#pragma unroll
+            for (int i = 0; i < RT; ++i)
+#pragma unroll
+                for (int j = 0; j < CT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+            const int r = r0 + i;
+            if (R % RT != 0 && r >= R) continue;
+#pragma unroll
+            for (int j = 0; j < CT; ++j) {
+                const int c = c0 + j;
+                if (C % CT != 0 && c >= C) continue;
+                float v = sgn * acc[i][j];
+                if (D) v += D[r * ldd + c];
+                out[r * ldo + c] = v;
+            }
+        }
+    }
+    if constexpr (SYNC) g.sync();
+}
+
+// y[R] = d + sgn * op(A) x   (matrix-vector, a one-column mm)
+template <int R, int K, bool TA, int NT, bool SYNC = true>
+__device__ __forceinline__ void mv(const Grp<NT>& g, float* y, const float* A, int lda,
+                                   const float* x, const float* d = nullptr, float sgn = 1.f)
+{
+    mm<R, 1, K, TA, false, NT, SYNC>(g, y, 1, A, lda, x, 1, d, 1, sgn);
+}
+
+// dst[R][C] = src (optionally transposed source)
+template <int R, int C, bool TS, int NT, bool SYNC = true>
+__device__ __forceinline__ void copy(const Grp<NT>& g, float* dst, int ldd, const float* src, int lds)
+{
+    for (int e = g.t; e < R * C; e += NT) {
+        const int r = e / C, c = e % C;
+        dst[r * ldd + c] = TS ? src[c * lds + r] : src[r * lds + c];
+    }
+    if constexpr (SYNC) g.sync();
+}
+
+template <int R, int C, int NT, bool SYNC = true>
+__device__ __forceinline__ void fill(const Grp<NT>& g, float* dst, int ldd, float v, float diag = 0.f)
+{
+    for (int e = g.t; e < R * C; e += NT) {
+        const int r = e / C, c = e % C;
+        dst[r * ldd + c] = (r == c) ? diag : v;
+    }
+    if constexpr (SYNC) g.sync();
+}
+
+// M <- (M + M^T) / 2 for an N x N matrix (removes rounding asymmetry).
+template <int N, int NT, bool SYNC = true>
+__device__ __forceinline__ void symmetrize(const Grp<NT>& g, float* M, int ld)
+{
+    for (int e = g.t; e < N * N; e += NT) {
+        const int r = e / N, c = e % N;
+        if (c > r) {
+            const float v = 0.5f * (M[r * ld + c] + M[c * ld + r]);
+            M[r * ld + c] = v;
+            M[c * ld + r] = v;
+        }
+    }
+    if constexpr (SYNC) g.sync();
+}
+
+// In-place Cholesky of an SPD M x M matrix (lower triangle, right-looking).
+// dinv[j] receives 1 / L[j][j].  Returns false (uniformly over the group) if
+// a pivot is not positive and finite; the factor is then meaningless.
+template <int M, int NT>
+__device__ bool chol(const Grp<NT>& g, float* L, int ld, float* dinv)
+{
+    bool ok = true;
+    for (int j = 0; j < M; ++j) {
+        const float d = L[j * ld + j];
+        ok = ok && (d > 0.f) && isfinite(d);
+        const float s = sqrtf(fmaxf(d, 1e-30f));
+        const float inv = 1.f / s;
+        g.sync();
+        for (int i = j + 1 + g.t; i < M; i += NT) L[i * ld + j] *= inv;
+        if (g.t == 0) {
+            L[j * ld + j] = s;
+            dinv[j] = inv;
+        }
+        g.sync();
+        const int rem = M - j - 1;
+        for (int e = g.t; e < rem * rem; e += NT) {
+            const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+            if (k <= i) L[i * ld + k] -= L[i * ld + j] * L[k * ld + j];
+        }
+        g.sync();
+    }
+    return ok;
+}
+
+// Solve L Y = X in place (X is M x NC); L lower triangular, dinv = 1/diag.
+template <int M, int NC, int NT>
+__device__ void trsm_lower(const Grp<NT>& g, const float* L, int ld, const float* dinv,
+                           float* X, int ldx)
+{
+    for (int i = 0; i < M; ++i) {
+        for (int c = g.t; c < NC; c += NT) X[i * ldx + c] *= dinv[i];
+        g.sync();
+        const int rows = M - i - 1;
+        for (int e = g.t; e < rows * NC; e += NT) {
+            const int r = i + 1 + e / NC, c = e % NC;
+            X[r * ldx + c] -= L[r * ld + i] * X[i * ldx + c];
+        }
+        g.sync();
+    }
+}
+
+// Solve L^T Y = X in place (X is M x NC).
+template <int M, int NC, int NT>
+__device__ void trsm_lower_t(const Grp<NT>& g, const float* L, int ld, const float* dinv,
+                             float* X, int ldx)
+{
+    for (int i = M - 1; i >= 0; --i) {
+        for (int c = g.t; c < NC; c += NT) X[i * ldx + c] *= dinv[i];
+        g.sync();
+        for (int e = g.t; e < i * NC; e += NT) {
+            const int r = e / NC, c = e % NC;
+            X[r * ldx + c] -= L[i * ld + r] * X[i * ldx + c];
+        }
+        g.sync();
+    }
+}
+
+// Gauss-Jordan elimination with partial pivoting on the augmented matrix
+// [Mx | RHS] (Mx is N x N in columns 0..N-1, NR right-hand sides after it).
+// On exit columns N..N+NR-1 hold Mx^{-1} RHS.  Returns false (uniformly) if
+// a pivot is zero or not finite.
+template <int N, int NR, int NT>
+__device__ bool gj_solve(const Grp<NT>& g, float* G, int ld)
+{
+    constexpr int W = N + NR;
+    bool ok = true;
+    for (int k = 0; k < N; ++k) {
+        int piv = k;
+        float best = fabsf(G[k * ld + k]);
+        for (int i = k + 1; i < N; ++i) {
+            const float v = fabsf(G[i * ld + k]);
+            if (v > best) { best = v; piv = i; }
+        }
+        ok = ok && (best > 1e-30f) && isfinite(best);
+        if (piv != k) {  // uniform: every thread saw the same column
+            g.sync();
+            for (int j = k + g.t; j < W; j += NT) {
+                const float a = G[k * ld + j];
+                G[k * ld + j] = G[piv * ld + j];
+                G[piv * ld + j] = a;
+            }
+            g.sync();
+        }
+        const float inv = 1.f / G[k * ld + k];
+        for (int j = k + 1 + g.t; j < W; j += NT) G[k * ld + j] *= inv;
+        g.sync();
+        const int cols = W - k - 1;
+        for (int e = g.t; e < (N - 1) * cols; e += NT) {
+            const int ii = e / cols;
+            const int i = ii + (ii >= k ? 1 : 0);
+            const int j = k + 1 + e % cols;
+            G[i * ld + j] -= G[i * ld + k] * G[k * ld + j];
+        }
+        g.sync();
+    }
+    return ok;
+}
+
+}  // namespace pdl

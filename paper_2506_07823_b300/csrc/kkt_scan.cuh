@@ -1,0 +1,580 @@
+// kkt_scan.cuh -- LQ KKT solve of one primal-dual iLQR step on the GPU.
+//
+// Two solvers share the stage-level building blocks below:
+//
+//  * kkt_scan_kernel  -- the parallel associative scan of Sec. II-D.  One CTA
+//    owns one instance; its W warps split the N+1 stages into W contiguous
+//    chunks.  The reverse scan is a reduce-then-scan:
+//      phase 1  middle chunks fold their CVF elements (Eq. initialization)
+//               with the combine of Eq. (combination_rule) into one aggregate
+//               per chunk, while the last chunk runs the value-function
+//               recursion from the terminal cost;
+//      phase 2  a Hillis-Steele suffix scan over the chunk aggregates gives
+//               the value function (P, p) at every chunk boundary;
+//      phase 3  every chunk walks its stages backwards from its boundary
+//               value function: e_k (x) V_{k+1} is evaluated in its Riccati
+//               form (Eq. lqr), which also yields the policy K_k, k_k of the
+//               "one pass in parallel" recovery, and the chunk's closed-loop
+//               affine map (Abar, bbar) of Eq. (controlled_dynamics);
+//      phase 4  the trajectory scan: the chunk affine maps are composed from
+//               dx_0, then each chunk rolls dx, du and dlam = P dx + p out.
+//  * riccati_kernel   -- the sequential Riccati recursion (Eq. lqr) and
+//    forward rollout, one warp per instance: the comparator.
+//
+// The combine uses the corrected rule (typos of the printed rule fixed):
+//   M = I + C1 P2,
+//   A = A2 M^-1 A1,            b = A2 M^-1 (b1 - C1 p2) + b2,
+//   C = A2 M^-1 C1 A2^T + C2,  P = (M^-1 A1)^T P2 A1 + P1,
+//   p = (M^-1 A1)^T (p2 + P2 b1) + p1,
+// with M^-1 applied by Gauss-Jordan elimination with partial pivoting.
+#pragma once
+
+#include "dev_linalg.cuh"
+
+namespace pdl {
+
+// Status codes written per instance (mirror the C ABI's pdilqr_status).
+enum : int32_t { ST_OK = 0, ST_NOT_SPD = 2, ST_SINGULAR = 3, ST_NONFINITE = 4 };
+
+struct KktArgs {
+    const float *A, *B, *c, *Q, *R, *S, *q, *r;  // LQ data; S may be null (S = 0)
+    const float* s;                              // [count][n] dx_0
+    float *dx, *du, *dlam;                       // outputs, N+1 stage slots
+    float *K, *k, *P, *p;                        // policy and value function per stage
+    float *Abar, *bbar;                          // closed-loop maps per stage
+    const int32_t* N;                            // [count] horizon
+    const int64_t* off;                          // [count] first stage slot
+    const int32_t* order;                        // [count] CTA -> instance (longest first)
+    int32_t* status;                             // [count]
+    int count;
+};
+
+// ------------------------------------------------------------------ layouts
+template <int NX, int NU>
+struct StageL {  // one stage of LQ data staged in shared memory
+    static constexpr int A = 0, B = A + NX * NX, Q = B + NX * NU, R = Q + NX * NX,
+                         S = R + NU * NU, c = S + NU * NX, q = c + NX, r = q + NX,
+                         SIZE = round4(r + NU);
+};
+
+template <int NX>
+struct ElemL {  // CVF element (A, C, b, P, p); a value function uses P, p only,
+                // which are contiguous so that it copies as one block
+    static constexpr int A = 0, C = NX * NX, b = 2 * NX * NX, P = 2 * NX * NX + NX,
+                         p = 3 * NX * NX + NX, SIZE = round4(3 * NX * NX + 2 * NX);
+};
+
+template <int NX, int NU>
+struct BuildL {  // scratch of the element build
+    static constexpr int Lr = 0, dinv = Lr + NU * NU, Z = round4(dinv + NU),
+                         Y = Z + NU * NX, SIZE = round4(Y + NU * (NX + 1));
+};
+
+template <int NX>
+struct CombL {  // scratch of a combine
+    static constexpr int LDG = 3 * NX + 1;
+    static constexpr int G = 0, T = round4(NX * LDG), U = T + NX * NX, w = U + NX * NX,
+                         SIZE = round4(w + NX);
+};
+
+template <int NX, int NU>
+struct RicL {  // scratch of one Riccati step
+    static constexpr int PB = 0, PA = PB + NX * NU, w = PA + NX * NX, G = round4(w + NX),
+                         dinv = G + NU * NU, Y = round4(dinv + NU), Y2 = Y + NU * (NX + 1),
+                         SIZE = round4(Y2 + NU * (NX + 1));
+};
+
+// ------------------------------------------------------------ stage loading
+template <int NX, int NU, int NT>
+__device__ __forceinline__ void load_stage(const Grp<NT>& g, float* st, const KktArgs& a,
+                                           int64_t gs, bool terminal)
+{
+    using L = StageL<NX, NU>;
+    const float* srcQ = a.Q + gs * NX * NX;
+    for (int e = g.t; e < NX * NX; e += NT) st[L::Q + e] = srcQ[e];
+    for (int e = g.t; e < NX; e += NT) st[L::q + e] = a.q[gs * NX + e];
+    if (!terminal) {
+        const float* srcA = a.A + gs * NX * NX;
+        const float* srcB = a.B + gs * NX * NU;
+        const float* srcR = a.R + gs * NU * NU;
+        for (int e = g.t; e < NX * NX; e += NT) st[L::A + e] = srcA[e];
+        for (int e = g.t; e < NX * NU; e += NT) st[L::B + e] = srcB[e];
+        for (int e = g.t; e < NU * NU; e += NT) st[L::R + e] = srcR[e];
+        for (int e = g.t; e < NX; e += NT) st[L::c + e] = a.c[gs * NX + e];
+        for (int e = g.t; e < NU; e += NT) st[L::r + e] = a.r[gs * NU + e];
+        if (a.S) {
+            const float* srcS = a.S + gs * NU * NX;
+            for (int e = g.t; e < NU * NX; e += NT) st[L::S + e] = srcS[e];
+        }
+    }
+    g.sync();
+}
+
+// ------------------------------------------------------------ element build
+// e_k = (A - B R^-1 S, c - B R^-1 r, B R^-1 B^T, q - S^T R^-1 r, Q - S^T R^-1 S)
+// (Eq. initialization); the terminal element is (0, 0, 0, q_N, Q_N).
+template <int NX, int NU, int NT>
+__device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float* scr,
+                              bool has_S, bool terminal)
+{
+    using L = StageL<NX, NU>;
+    using E = ElemL<NX>;
+    using S = BuildL<NX, NU>;
+    if (terminal) {
+        fill<NX, NX, NT, false>(g, e + E::A, NX, 0.f);
+        fill<NX, NX, NT, false>(g, e + E::C, NX, 0.f);
+        for (int i = g.t; i < NX; i += NT) { e[E::b + i] = 0.f; e[E::p + i] = st[L::q + i]; }
+        copy<NX, NX, false, NT>(g, e + E::P, NX, st + L::Q, NX);
+        return true;
+    }
+    float* Lr = scr + S::Lr;
+    float* dinv = scr + S::dinv;
+    float* Z = scr + S::Z;
+    float* Y = scr + S::Y;
+    constexpr int LDY = NX + 1;
+    copy<NU, NU, false, NT, false>(g, Lr, NU, st + L::R, NU);
+    copy<NU, NX, true, NT, false>(g, Z, NX, st + L::B, NU);   // Z = B^T
+    if (has_S) copy<NU, NX, false, NT, false>(g, Y, LDY, st + L::S, NX);
+    for (int i = g.t; i < NU; i += NT) Y[i * LDY + NX] = st[L::r + i];
+    g.sync();
+    const bool ok = chol<NU, NT>(g, Lr, NU, dinv);
+    trsm_lower<NU, NX, NT>(g, Lr, NU, dinv, Z, NX);             // Z = L^-1 B^T
+    if (has_S) {
+        trsm_lower<NU, NX + 1, NT>(g, Lr, NU, dinv, Y, LDY);
+        trsm_lower_t<NU, NX + 1, NT>(g, Lr, NU, dinv, Y, LDY);  // Y = R^-1 [S | r]
+    } else {
+        trsm_lower<NU, 1, NT>(g, Lr, NU, dinv, Y + NX, LDY);
+        trsm_lower_t<NU, 1, NT>(g, Lr, NU, dinv, Y + NX, LDY);  // y = R^-1 r
+    }
+    mm<NX, NX, NU, true, false, NT, false>(g, e + E::C, NX, Z, NX, Z, NX);  // C = Z^T Z
+    mm<NX, 1, NU, false, false, NT, false>(g, e + E::b, 1, st + L::B, NU, Y + NX, LDY,
+                                           st + L::c, 1, -1.f);            // b = c - B y
+    if (has_S) {
+        mm<NX, NX, NU, false, false, NT, false>(g, e + E::A, NX, st + L::B, NU, Y, LDY,
+                                                st + L::A, NX, -1.f);
+        mm<NX, NX, NU, true, false, NT, false>(g, e + E::P, NX, st + L::S, NX, Y, LDY,
+                                               st + L::Q, NX, -1.f);
+        mm<NX, 1, NU, true, false, NT, false>(g, e + E::p, 1, st + L::S, NX, Y + NX, LDY,
+                                              st + L::q, 1, -1.f);
+    } else {
+        copy<NX, NX, false, NT, false>(g, e + E::A, NX, st + L::A, NX);
+        copy<NX, NX, false, NT, false>(g, e + E::P, NX, st + L::Q, NX);
+        for (int i = g.t; i < NX; i += NT) e[E::p + i] = st[L::q + i];
+    }
+    g.sync();
+    return ok;
+}
+
+// ----------------------------------------------------------------- combines
+// out = e1 (x) e2 for two full elements (e1 earlier in time).  out must not
+// alias e1 or e2.
+template <int NX, int NT>
+__device__ bool combine_full(const Grp<NT>& g, const float* e1, const float* e2, float* out,
+                             float* scr)
+{
+    using E = ElemL<NX>;
+    using S = CombL<NX>;
+    constexpr int LDG = S::LDG;
+    float* G = scr + S::G;
+    float* T = scr + S::T;
+    float* U = scr + S::U;
+    float* w = scr + S::w;
+    // G = [C1 P2 | A1 | C1 | b1 - C1 p2];  U = P2 A1;  w = p2 + P2 b1
+    mm<NX, NX, NX, false, false, NT, false>(g, G, LDG, e1 + E::C, NX, e2 + E::P, NX);
+    copy<NX, NX, false, NT, false>(g, G + NX, LDG, e1 + E::A, NX);
+    copy<NX, NX, false, NT, false>(g, G + 2 * NX, LDG, e1 + E::C, NX);
+    mm<NX, 1, NX, false, false, NT, false>(g, G + 3 * NX, LDG, e1 + E::C, NX, e2 + E::p, 1,
+                                           e1 + E::b, 1, -1.f);
+    mm<NX, NX, NX, false, false, NT, false>(g, U, NX, e2 + E::P, NX, e1 + E::A, NX);
+    mm<NX, 1, NX, false, false, NT, false>(g, w, 1, e2 + E::P, NX, e1 + E::b, 1, e2 + E::p, 1);
+    g.sync();
+    for (int i = g.t; i < NX; i += NT) G[i * LDG + i] += 1.f;   // M = I + C1 P2
+    g.sync();
+    const bool ok = gj_solve<NX, 2 * NX + 1, NT>(g, G, LDG);
+    const float* XA = G + NX;       // M^-1 A1
+    const float* XC = G + 2 * NX;   // M^-1 C1
+    const float* xb = G + 3 * NX;   // M^-1 (b1 - C1 p2)
+    mm<NX, NX, NX, false, false, NT, false>(g, out + E::A, NX, e2 + E::A, NX, XA, LDG);
+    mm<NX, 1, NX, false, false, NT, false>(g, out + E::b, 1, e2 + E::A, NX, xb, LDG,
+                                           e2 + E::b, 1);
+    mm<NX, NX, NX, false, false, NT, false>(g, T, NX, e2 + E::A, NX, XC, LDG);
+    mm<NX, NX, NX, true, false, NT, false>(g, out + E::P, NX, XA, LDG, U, NX, e1 + E::P, NX);
+    mm<NX, 1, NX, true, false, NT, false>(g, out + E::p, 1, XA, LDG, w, 1, e1 + E::p, 1);
+    g.sync();
+    mm<NX, NX, NX, false, true, NT>(g, out + E::C, NX, T, NX, e2 + E::A, NX, e2 + E::C, NX);
+    symmetrize<NX, NT, false>(g, out + E::C, NX);
+    symmetrize<NX, NT>(g, out + E::P, NX);
+    return ok;
+}
+
+// out(P, p) = e1 (x) V2 where V2 is a value function (A2 = C2 = b2 = 0):
+// P = (M^-1 A1)^T P2 A1 + P1,  p = (M^-1 A1)^T (p2 + P2 b1) + p1.
+template <int NX, int NT>
+__device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, float* out,
+                           float* scr)
+{
+    using E = ElemL<NX>;
+    using S = CombL<NX>;
+    constexpr int LDG = 2 * NX;
+    float* G = scr + S::G;
+    float* U = scr + S::U;
+    float* w = scr + S::w;
+    mm<NX, NX, NX, false, false, NT, false>(g, G, LDG, e1 + E::C, NX, v2 + E::P, NX);
+    copy<NX, NX, false, NT, false>(g, G + NX, LDG, e1 + E::A, NX);
+    mm<NX, NX, NX, false, false, NT, false>(g, U, NX, v2 + E::P, NX, e1 + E::A, NX);
+    mm<NX, 1, NX, false, false, NT, false>(g, w, 1, v2 + E::P, NX, e1 + E::b, 1, v2 + E::p, 1);
+    g.sync();
+    for (int i = g.t; i < NX; i += NT) G[i * LDG + i] += 1.f;
+    g.sync();
+    const bool ok = gj_solve<NX, NX, NT>(g, G, LDG);
+    const float* XA = G + NX;
+    mm<NX, NX, NX, true, false, NT, false>(g, out + E::P, NX, XA, LDG, U, NX, e1 + E::P, NX);
+    mm<NX, 1, NX, true, false, NT, false>(g, out + E::p, 1, XA, LDG, w, 1, e1 + E::p, 1);
+    g.sync();
+    symmetrize<NX, NT>(g, out + E::P, NX);
+    return ok;
+}
+
+// ------------------------------------------------------------ Riccati step
+// Given V_{k+1} = (P', p') and stage k, evaluate Eq. (lqr):
+//   G = R + B^T P' B,  H = S + B^T P' A,  h = B^T (p' + P' c) + r,
+//   K = -G^-1 H,  k = -G^-1 h,
+//   P = Q + A^T P' A + K^T H,  p = q + A^T (p' + P' c) + K^T h,
+// using the Cholesky factor G = L L^T: with [Z | z] = L^-1 [H | h],
+// K^T H = -Z^T Z and K^T h = -Z^T z.  Writes P, p into vout (SMEM) and K, k,
+// P, p, Abar = A + B K, bbar = B k + c to global memory at stage gs.
+template <int NX, int NU, int NT>
+__device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin, float* vout,
+                             float* scr, const KktArgs& a, int64_t gs)
+{
+    using L = StageL<NX, NU>;
+    using E = ElemL<NX>;
+    using S = RicL<NX, NU>;
+    constexpr int LDY = NX + 1;
+    float* PB = scr + S::PB;
+    float* PA = scr + S::PA;
+    float* w = scr + S::w;
+    float* Gm = scr + S::G;
+    float* dinv = scr + S::dinv;
+    float* Y = scr + S::Y;
+    float* Y2 = scr + S::Y2;
+    const float* P1 = vin + E::P;
+    const float* p1 = vin + E::p;
+    mm<NX, NU, NX, false, false, NT, false>(g, PB, NU, P1, NX, st + L::B, NU);
+    mm<NX, NX, NX, false, false, NT, false>(g, PA, NX, P1, NX, st + L::A, NX);
+    mm<NX, 1, NX, false, false, NT, false>(g, w, 1, P1, NX, st + L::c, 1, p1, 1);
+    g.sync();
+    mm<NU, NU, NX, true, false, NT, false>(g, Gm, NU, st + L::B, NU, PB, NU, st + L::R, NU);
+    mm<NU, NX, NX, true, false, NT, false>(g, Y, LDY, st + L::B, NU, PA, NX,
+                                           a.S ? st + L::S : nullptr, NX);
+    mm<NU, 1, NX, true, false, NT, false>(g, Y + NX, LDY, st + L::B, NU, w, 1, st + L::r, 1);
+    g.sync();
+    const bool ok = chol<NU, NT>(g, Gm, NU, dinv);
+    trsm_lower<NU, NX + 1, NT>(g, Gm, NU, dinv, Y, LDY);           // [Z | z]
+    copy<NU, NX + 1, false, NT>(g, Y2, LDY, Y, LDY);
+    trsm_lower_t<NU, NX + 1, NT>(g, Gm, NU, dinv, Y2, LDY);        // G^-1 [H | h]
+    // P = Q + A^T (P' A) - Z^T Z ;  p = q + A^T w - Z^T z
+    float* P = vout + E::P;
+    float* p = vout + E::p;
+    mm<NX, NX, NX, true, false, NT, false>(g, P, NX, st + L::A, NX, PA, NX, st + L::Q, NX);
+    mm<NX, 1, NX, true, false, NT, false>(g, p, 1, st + L::A, NX, w, 1, st + L::q, 1);
+    g.sync();
+    mm<NX, NX, NU, true, false, NT, false>(g, P, NX, Y, LDY, Y, LDY, P, NX, -1.f);
+    mm<NX, 1, NU, true, false, NT, false>(g, p, 1, Y, LDY, Y + NX, LDY, p, 1, -1.f);
+    // K = -Y2[:, :NX], k = -Y2[:, NX];  Abar = A + B K;  bbar = B k + c
+    float* Kg = a.K + gs * NU * NX;
+    float* kg = a.k + gs * NU;
+    for (int e = g.t; e < NU * NX; e += NT) Kg[e] = -Y2[(e / NX) * LDY + (e % NX)];
+    for (int i = g.t; i < NU; i += NT) kg[i] = -Y2[i * LDY + NX];
+    mm<NX, NX, NU, false, false, NT, false>(g, a.Abar + gs * NX * NX, NX, st + L::B, NU, Y2, LDY,
+                                            st + L::A, NX, -1.f);
+    mm<NX, 1, NU, false, false, NT, false>(g, a.bbar + gs * NX, 1, st + L::B, NU, Y2 + NX, LDY,
+                                           st + L::c, 1, -1.f);
+    g.sync();
+    symmetrize<NX, NT>(g, P, NX);
+    float* Pg = a.P + gs * NX * NX;
+    float* pg = a.p + gs * NX;
+    for (int e = g.t; e < NX * NX; e += NT) Pg[e] = P[e];
+    for (int i = g.t; i < NX; i += NT) pg[i] = p[i];
+    return ok;
+}
+
+// Terminal stage: V_N = (Q_N, q_N), K_N = 0, k_N = 0.
+template <int NX, int NU, int NT>
+__device__ void terminal_value(const Grp<NT>& g, const float* st, float* vout, const KktArgs& a,
+                               int64_t gs)
+{
+    using L = StageL<NX, NU>;
+    using E = ElemL<NX>;
+    for (int e = g.t; e < NX * NX; e += NT) {
+        vout[E::P + e] = st[L::Q + e];
+        a.P[gs * NX * NX + e] = st[L::Q + e];
+    }
+    for (int i = g.t; i < NX; i += NT) {
+        vout[E::p + i] = st[L::q + i];
+        a.p[gs * NX + i] = st[L::q + i];
+    }
+    for (int e = g.t; e < NU * NX; e += NT) a.K[gs * NU * NX + e] = 0.f;
+    for (int i = g.t; i < NU; i += NT) a.k[gs * NU + i] = 0.f;
+    g.sync();
+}
+
+// Roll the trajectory of stages [k0, k1) forward from x (SMEM, length NX):
+// dx_k = x, du_k = K_k x + k_k, dlam_k = P_k x + p_k, x <- Abar_k x + bbar_k.
+template <int NX, int NU, int NT>
+__device__ void rollout_chunk(const Grp<NT>& g, float* x, float* xn, const KktArgs& a,
+                              int64_t off, int N, int k0, int k1)
+{
+    for (int k = k0; k < k1; ++k) {
+        const int64_t gs = off + k;
+        for (int i = g.t; i < NX; i += NT) a.dx[gs * NX + i] = x[i];
+        mv<NX, NX, false, NT, false>(g, a.dlam + gs * NX, a.P + gs * NX * NX, NX, x,
+                                     a.p + gs * NX);
+        if (k < N) {
+            mv<NU, NX, false, NT, false>(g, a.du + gs * NU, a.K + gs * NU * NX, NX, x,
+                                         a.k + gs * NU);
+            mv<NX, NX, false, NT, false>(g, xn, a.Abar + gs * NX * NX, NX, x, a.bbar + gs * NX);
+            g.sync();
+            for (int i = g.t; i < NX; i += NT) x[i] = xn[i];
+        } else {
+            for (int i = g.t; i < NU; i += NT) a.du[gs * NU + i] = 0.f;
+        }
+        g.sync();
+    }
+}
+
+// ---------------------------------------------------------- chunk partition
+// Chunk w of W over S = N+1 stages: every chunk gets one stage, the rest is
+// shared in proportion to weights 10 (first and middle chunks) and 16 (the
+// last chunk, whose value-function recursion runs while the middle chunks
+// fold the costlier full combines).
+__device__ __forceinline__ int chunk_start(int w, int W, int S)
+{
+    if (w >= W) return S;
+    const int units = (W - 1) * 10 + 16;
+    const int extra = S - W;
+    return w + (int)(((int64_t)extra * (w * 10)) / units);
+}
+
+// ------------------------------------------------------------- scan kernel
+template <int NX, int NU, int W>
+struct ScanSmem {
+    static constexpr int ELEM = ElemL<NX>::SIZE;
+    static constexpr int STG = StageL<NX, NU>::SIZE;
+    // phase 1 (middle chunk): stage | elem | tmpE | build/combine scratch
+    static constexpr int P1 = STG + 2 * ELEM +
+                              (BuildL<NX, NU>::SIZE > CombL<NX>::SIZE ? BuildL<NX, NU>::SIZE
+                                                                      : CombL<NX>::SIZE);
+    // phase 1 (last chunk) / phase 3: stage | V0 | V1 | riccati scratch | Psi0 | Psi1 | psi
+    static constexpr int PSI = round4(2 * ELEM + STG + RicL<NX, NU>::SIZE);
+    static constexpr int P3 = PSI + 2 * NX * NX + round4(NX) * 2;
+    static constexpr int PRIV = round4(P1 > P3 ? P1 : P3);
+    static constexpr int SLOTS = W * ELEM;
+    static constexpr int XS = W * round4(NX);
+    static constexpr int TOTAL = SLOTS + W * PRIV + XS + 4;  // + status words
+    static constexpr size_t BYTES = sizeof(float) * TOTAL;
+};
+
+template <int NX, int NU, int W>
+__global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
+{
+    using SM = ScanSmem<NX, NU, W>;
+    using E = ElemL<NX>;
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5;
+    const Grp<32> g{(int)(threadIdx.x & 31), 0};
+    const int inst = a.order ? a.order[blockIdx.x] : blockIdx.x;
+    if (inst >= a.count) return;
+    const int N = a.N[inst];
+    const int64_t off = a.off[inst];
+    const int S = N + 1;
+    const int Weff = W < S ? W : S;
+    const bool has_S = a.S != nullptr;
+
+    float* slots = smem;                               // [W][ELEM]
+    float* priv = smem + SM::SLOTS + warp * SM::PRIV;  // this warp's private area
+    float* xs = smem + SM::SLOTS + W * SM::PRIV;       // [W][NX] chunk start states
+    int* st_word = reinterpret_cast<int*>(xs + SM::XS);
+    if (threadIdx.x == 0) st_word[0] = ST_OK;
+    __syncthreads();
+
+    const int k0 = chunk_start(warp, Weff, S);
+    const int k1 = chunk_start(warp + 1, Weff, S);
+    const bool active = warp < Weff;
+    const bool last = warp == Weff - 1;
+    int bad = ST_OK;
+
+    // ---- phase 1
+    float* stg = priv;
+    if (active && !last && warp > 0) {
+        // fold e_{k0} (x) ... (x) e_{k1-1} into slots[warp]
+        float* elem = priv + SM::STG;
+        float* tmpE = elem + SM::ELEM;
+        float* scr = tmpE + SM::ELEM;
+        float* acc = slots + warp * SM::ELEM;
+        float* other = tmpE;
+        for (int k = k0; k < k1; ++k) {
+            load_stage<NX, NU, 32>(g, stg, a, off + k, false);
+            if (k == k0) {
+                if (!build_element<NX, NU, 32>(g, stg, acc, scr, has_S, false)) bad = ST_NOT_SPD;
+            } else {
+                if (!build_element<NX, NU, 32>(g, stg, elem, scr, has_S, false)) bad = ST_NOT_SPD;
+                if (!combine_full<NX, 32>(g, acc, elem, other, scr)) bad = ST_SINGULAR;
+                float* t = acc; acc = other; other = t;
+            }
+        }
+        if (acc != slots + warp * SM::ELEM) copy<E::SIZE, 1, false, 32>(g, slots + warp * SM::ELEM, 1, acc, 1);
+    } else if (active && last) {
+        // value-function recursion of the last chunk from the terminal cost
+        float* v0 = priv + SM::STG;
+        float* v1 = v0 + SM::ELEM;
+        float* scr = v1 + SM::ELEM;
+        for (int k = k1 - 1; k >= k0; --k) {
+            load_stage<NX, NU, 32>(g, stg, a, off + k, k == N);
+            if (k == N) {
+                terminal_value<NX, NU, 32>(g, stg, v0, a, off + k);
+            } else {
+                if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, off + k)) bad = ST_NOT_SPD;
+                float* t = v0; v0 = v1; v1 = t;
+            }
+        }
+        copy<E::SIZE, 1, false, 32>(g, slots + warp * SM::ELEM, 1, v0, 1);
+    }
+    __syncthreads();
+
+    // ---- phase 2: suffix scan over chunk slots 1..Weff-1 (slot Weff-1 is a
+    // value function); slot j ends up holding the value function at the start
+    // of chunk j.
+    {
+        const int J = Weff - 1;     // items 0..J-1 live in slots 1..Weff-1
+        const int j = warp - 1;
+        float* res = priv + SM::STG;             // private result buffer
+        float* scr = res + SM::ELEM;
+        for (int d = 1; d < J; d <<= 1) {
+            const bool act = (j >= 0) && (j + d < J);
+            bool vf = false;
+            if (act) {
+                vf = (j + 2 * d - 1 >= J - 1);
+                const float* e1 = slots + (j + 1) * SM::ELEM;
+                const float* e2 = slots + (j + 1 + d) * SM::ELEM;
+                const bool ok = vf ? combine_vf<NX, 32>(g, e1, e2, res, scr)
+                                   : combine_full<NX, 32>(g, e1, e2, res, scr + SM::ELEM);
+                if (!ok) bad = ST_SINGULAR;
+            }
+            __syncthreads();
+            if (act) {
+                float* dst = slots + (j + 1) * SM::ELEM;
+                if (vf) {
+                    copy<NX * NX + NX, 1, false, 32>(g, dst + E::P, 1, res + E::P, 1);
+                } else {
+                    copy<E::SIZE, 1, false, 32>(g, dst, 1, res, 1);
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- phase 3: Riccati sweep of chunks 0..Weff-2 from their boundary
+    // value functions, composing the chunk's closed-loop affine map.
+    float* psiA = priv + SM::PSI;
+    float* psiB = psiA + NX * NX;
+    float* psiv = psiB + NX * NX;
+    float* psitmp = psiv + round4(NX);
+    if (active && !last) {
+        float* v0 = priv + SM::STG;
+        float* v1 = v0 + SM::ELEM;
+        float* scr = v1 + SM::ELEM;
+        copy<NX * NX + NX, 1, false, 32, false>(g, v0 + E::P, 1, slots + (warp + 1) * SM::ELEM + E::P, 1);
+        fill<NX, NX, 32, false>(g, psiA, NX, 0.f, 1.f);
+        for (int i = g.t; i < NX; i += 32) psiv[i] = 0.f;
+        g.sync();
+        for (int k = k1 - 1; k >= k0; --k) {
+            const int64_t gs = off + k;
+            load_stage<NX, NU, 32>(g, stg, a, gs, false);
+            if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, gs)) bad = ST_NOT_SPD;
+            float* t = v0; v0 = v1; v1 = t;
+            __threadfence_block();
+            g.sync();
+            // psi <- Psi bbar_k + psi ;  Psi <- Psi Abar_k
+            mm<NX, 1, NX, false, false, 32, false>(g, psitmp, 1, psiA, NX, a.bbar + gs * NX, 1, psiv, 1);
+            mm<NX, NX, NX, false, false, 32, false>(g, psiB, NX, psiA, NX, a.Abar + gs * NX * NX, NX);
+            g.sync();
+            for (int i = g.t; i < NX; i += 32) psiv[i] = psitmp[i];
+            float* t2 = psiA; psiA = psiB; psiB = t2;
+            g.sync();
+        }
+        // publish Psi, psi at fixed slots of this warp's area
+        if (psiA != priv + SM::PSI) copy<NX * NX, 1, false, 32>(g, priv + SM::PSI, 1, psiA, 1);
+    }
+    if (bad != ST_OK && g.t == 0) atomicMax(st_word, bad);
+    __syncthreads();
+
+    // ---- phase 4: trajectory scan.  Chunk start states from dx_0 through the
+    // chunk maps, then every chunk rolls out dx, du, dlam.
+    if (warp == 0) {
+        float* x = xs;
+        for (int i = g.t; i < NX; i += 32) x[i] = a.s[(int64_t)inst * NX + i];
+        g.sync();
+        for (int w = 0; w + 1 < Weff; ++w) {
+            const float* Psi = smem + SM::SLOTS + w * SM::PRIV + SM::PSI;
+            const float* psv = Psi + 2 * NX * NX;
+            mv<NX, NX, false, 32>(g, xs + (w + 1) * round4(NX), Psi, NX, xs + w * round4(NX), psv);
+        }
+    }
+    __syncthreads();
+    if (active) {
+        float* x = priv;                 // reuse the private area
+        float* xn = priv + round4(NX);
+        for (int i = g.t; i < NX; i += 32) x[i] = xs[warp * round4(NX) + i];
+        g.sync();
+        rollout_chunk<NX, NU, 32>(g, x, xn, a, off, N, k0, k1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.status[inst] = st_word[0];
+}
+
+// --------------------------------------------------------- Riccati kernel
+template <int NX, int NU>
+struct RicSmem {
+    static constexpr int ELEM = ElemL<NX>::SIZE;
+    static constexpr int STG = StageL<NX, NU>::SIZE;
+    static constexpr int TOTAL = STG + 2 * ELEM + RicL<NX, NU>::SIZE + 2 * round4(NX);
+    static constexpr size_t BYTES = sizeof(float) * TOTAL;
+};
+
+// One warp per instance; blockDim.x = 32 * warps-per-block.
+template <int NX, int NU>
+__global__ void __launch_bounds__(128) riccati_kernel(KktArgs a)
+{
+    using SM = RicSmem<NX, NU>;
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5;
+    const int slot = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (slot >= a.count) return;
+    const int inst = a.order ? a.order[slot] : slot;
+    const Grp<32> g{(int)(threadIdx.x & 31), 0};
+    float* base = smem + warp * SM::TOTAL;
+    float* stg = base;
+    float* v0 = base + SM::STG;
+    float* v1 = v0 + SM::ELEM;
+    float* scr = v1 + SM::ELEM;
+    float* x = scr + RicL<NX, NU>::SIZE;
+    float* xn = x + round4(NX);
+    const int N = a.N[inst];
+    const int64_t off = a.off[inst];
+    int bad = ST_OK;
+    load_stage<NX, NU, 32>(g, stg, a, off + N, true);
+    terminal_value<NX, NU, 32>(g, stg, v0, a, off + N);
+    for (int k = N - 1; k >= 0; --k) {
+        load_stage<NX, NU, 32>(g, stg, a, off + k, false);
+        if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, off + k)) bad = ST_NOT_SPD;
+        float* t = v0; v0 = v1; v1 = t;
+    }
+    __threadfence_block();
+    for (int i = g.t; i < NX; i += 32) x[i] = a.s[(int64_t)inst * NX + i];
+    g.sync();
+    rollout_chunk<NX, NU, 32>(g, x, xn, a, off, N, 0, N + 1);
+    if (g.t == 0) a.status[inst] = bad;
+}
+
+}  // namespace pdl

@@ -1,0 +1,388 @@
+// pdilqr.cu -- C ABI of the LQ KKT solvers (plans, validation, dispatch).
+#include "pdilqr.h"
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kkt_scan.cuh"
+#include "residual.cuh"
+
+using namespace pdl;
+
+// ------------------------------------------------------------------ status
+extern "C" const char* pdilqr_status_string(int s)
+{
+    switch (s) {
+        case PDILQR_OK: return "ok";
+        case PDILQR_E_INVALID_ARG: return "invalid argument";
+        case PDILQR_E_NOT_SPD: return "matrix not positive definite";
+        case PDILQR_E_SINGULAR: return "singular (I + C P) in a combine";
+        case PDILQR_E_NONFINITE: return "non-finite value";
+        case PDILQR_E_TIMEOUT: return "timeout";
+        case PDILQR_E_NO_MEMORY: return "out of memory";
+        case PDILQR_E_ADMISSION: return "admission refused";
+        case PDILQR_E_LINESEARCH: return "line search found no step";
+        case PDILQR_E_CUDA: return "CUDA error";
+        default: return "unknown status";
+    }
+}
+
+static pdilqr_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return PDILQR_OK;
+    if (e == cudaErrorMemoryAllocation) return PDILQR_E_NO_MEMORY;
+    return PDILQR_E_CUDA;
+}
+#define PD_CUDA(x)                                             \
+    do {                                                       \
+        cudaError_t e_ = (x);                                  \
+        if (e_ != cudaSuccess) return cuda_status(e_);         \
+    } while (0)
+
+// --------------------------------------------------------- per-size kernels
+struct SizeOps {
+    int n, m;
+    bool scan_ok;  // the scan kernel fits shared memory for this size
+    cudaError_t (*scan)(const KktArgs&, int warps, cudaStream_t);
+    cudaError_t (*riccati)(const KktArgs&, cudaStream_t);
+    cudaError_t (*resid)(const ResidArgs&, cudaStream_t);
+    size_t (*scan_smem)(int warps);
+};
+
+template <int NX, int NU, int W>
+static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
+{
+    using SM = ScanSmem<NX, NU, W>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kkt_scan_kernel<NX, NU, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SM::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kkt_scan_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static size_t scan_smem(int warps)
+{
+    switch (warps) {
+        case 4: return ScanSmem<NX, NU, 4>::BYTES;
+        case 8: return ScanSmem<NX, NU, 8>::BYTES;
+        case 16: return ScanSmem<NX, NU, 16>::BYTES;
+        default: return 0;
+    }
+}
+
+template <int NX, int NU>
+static cudaError_t launch_scan(const KktArgs& a, int warps, cudaStream_t st)
+{
+    switch (warps) {
+        case 4: return launch_scan_w<NX, NU, 4>(a, st);
+        case 8: return launch_scan_w<NX, NU, 8>(a, st);
+        case 16: return launch_scan_w<NX, NU, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NX, int NU>
+static cudaError_t launch_riccati(const KktArgs& a, cudaStream_t st)
+{
+    using SM = RicSmem<NX, NU>;
+    // warps (instances) per block: up to 4, as many as fit in shared memory
+    constexpr int FIT = (int)((227 * 1024) / SM::BYTES);
+    constexpr int WPB = FIT >= 4 ? 4 : (FIT >= 1 ? FIT : 1);
+    const size_t bytes = SM::BYTES * WPB;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(riccati_kernel<NX, NU>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int grid = (a.count + WPB - 1) / WPB;
+    riccati_kernel<NX, NU><<<grid, 32 * WPB, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static cudaError_t launch_resid(const ResidArgs& a, cudaStream_t st)
+{
+    const int64_t blocks = (a.total_stages + 7) / 8;
+    kkt_residual_kernel<NX, NU><<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static SizeOps make_ops()
+{
+    SizeOps o;
+    o.n = NX;
+    o.m = NU;
+    o.scan_ok = ScanSmem<NX, NU, 4>::BYTES <= 227 * 1024;
+    o.scan = launch_scan<NX, NU>;
+    o.riccati = launch_riccati<NX, NU>;
+    o.resid = launch_resid<NX, NU>;
+    o.scan_smem = scan_smem<NX, NU>;
+    return o;
+}
+
+static const SizeOps* find_ops(int n, int m)
+{
+    static const SizeOps table[] = {
+        make_ops<1, 1>(), make_ops<2, 1>(), make_ops<3, 2>(), make_ops<4, 2>(),
+        make_ops<12, 12>(), make_ops<36, 24>(),
+    };
+    for (const auto& o : table)
+        if (o.n == n && o.m == m) return &o;
+    return nullptr;
+}
+
+// -------------------------------------------------------------------- plan
+struct pdilqr_plan {
+    int n = 0, m = 0, count = 0, warps = 0, refine = 0, maxN = 0;
+    int64_t total = 0;
+    const SizeOps* ops = nullptr;
+    std::vector<void*> allocs;
+    int32_t* dN = nullptr;
+    int64_t* doff = nullptr;
+    int32_t* dorder = nullptr;
+    int64_t* dstage_inst = nullptr;
+    // policy / value function / closed-loop maps per stage
+    float *K = nullptr, *k = nullptr, *P = nullptr, *p = nullptr, *Abar = nullptr, *bbar = nullptr;
+    // refinement
+    float *rq = nullptr, *rr = nullptr, *rc = nullptr, *rs = nullptr;
+    float *ddx = nullptr, *ddu = nullptr, *ddl = nullptr, *dk = nullptr, *dp = nullptr;
+    double* norms = nullptr;
+    int32_t* st2 = nullptr;
+
+    template <typename T>
+    cudaError_t alloc(T** ptr, size_t count_) {
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, std::max<size_t>(count_, 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            allocs.push_back(v);
+            *ptr = static_cast<T*>(v);
+        }
+        return e;
+    }
+    ~pdilqr_plan() {
+        for (void* v : allocs) cudaFree(v);
+    }
+};
+
+static int pick_warps(int maxN)
+{
+    if (maxN >= 40) return 16;
+    if (maxN >= 12) return 8;
+    return 4;
+}
+
+static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdilqr_opts* o)
+{
+    pl->n = b->n;
+    pl->m = b->m;
+    pl->count = b->count;
+    pl->ops = find_ops(b->n, b->m);
+    if (!pl->ops) return PDILQR_E_INVALID_ARG;
+    std::vector<int32_t> hN(b->N, b->N + b->count);
+    std::vector<int64_t> hoff(b->stage_off, b->stage_off + b->count);
+    // validate horizons and non-overlapping slot ranges
+    std::vector<int32_t> by_off(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        if (hN[i] < 1 || hN[i] > 4096 || hoff[i] < 0) return PDILQR_E_INVALID_ARG;
+        by_off[i] = i;
+        pl->maxN = std::max(pl->maxN, hN[i]);
+        pl->total = std::max<int64_t>(pl->total, hoff[i] + hN[i] + 1);
+    }
+    std::sort(by_off.begin(), by_off.end(), [&](int x, int y) { return hoff[x] < hoff[y]; });
+    for (int i = 1; i < b->count; ++i) {
+        const int pa = by_off[i - 1], pb = by_off[i];
+        if (hoff[pa] + hN[pa] + 1 > hoff[pb]) return PDILQR_E_INVALID_ARG;
+    }
+    pl->warps = (o && o->warps) ? o->warps : pick_warps(pl->maxN);
+    if (pl->warps != 4 && pl->warps != 8 && pl->warps != 16) return PDILQR_E_INVALID_ARG;
+    pl->refine = (o && o->refine) ? 1 : 0;
+    // longest horizons first: the tail of the grid holds the short instances
+    std::vector<int32_t> order(b->count);
+    for (int i = 0; i < b->count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hN[x] > hN[y]; });
+    std::vector<int64_t> stage_inst(pl->total, -1);  // -1: slot of no instance
+    for (int i = 0; i < b->count; ++i)
+        for (int k = 0; k <= hN[i]; ++k) stage_inst[hoff[i] + k] = i;
+
+    const size_t n = pl->n, m = pl->m, T = pl->total, C = pl->count;
+    PD_CUDA(pl->alloc(&pl->dN, C));
+    PD_CUDA(pl->alloc(&pl->doff, C));
+    PD_CUDA(pl->alloc(&pl->dorder, C));
+    PD_CUDA(pl->alloc(&pl->dstage_inst, T));
+    PD_CUDA(pl->alloc(&pl->K, T * m * n));
+    PD_CUDA(pl->alloc(&pl->k, T * m));
+    PD_CUDA(pl->alloc(&pl->P, T * n * n));
+    PD_CUDA(pl->alloc(&pl->p, T * n));
+    PD_CUDA(pl->alloc(&pl->Abar, T * n * n));
+    PD_CUDA(pl->alloc(&pl->bbar, T * n));
+    PD_CUDA(pl->alloc(&pl->norms, C * 4));
+    PD_CUDA(pl->alloc(&pl->st2, C));
+    PD_CUDA(pl->alloc(&pl->rq, T * n));
+    PD_CUDA(pl->alloc(&pl->rr, T * m));
+    PD_CUDA(pl->alloc(&pl->rc, T * n));
+    PD_CUDA(pl->alloc(&pl->rs, C * n));
+    PD_CUDA(pl->alloc(&pl->ddx, T * n));
+    PD_CUDA(pl->alloc(&pl->ddu, T * m));
+    PD_CUDA(pl->alloc(&pl->ddl, T * n));
+    PD_CUDA(cudaMemcpy(pl->dN, hN.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(pl->doff, hoff.data(), C * sizeof(int64_t), cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(pl->dorder, order.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(pl->dstage_inst, stage_inst.data(), T * sizeof(int64_t),
+                       cudaMemcpyHostToDevice));
+    return PDILQR_OK;
+}
+
+extern "C" pdilqr_status pdilqr_plan_create(const pdilqr_batch* b, const pdilqr_opts* o,
+                                            pdilqr_plan** out)
+{
+    if (!out) return PDILQR_E_INVALID_ARG;
+    *out = nullptr;
+    if (!b || !b->N || !b->stage_off || b->count < 1 || b->n < 1 || b->m < 1)
+        return PDILQR_E_INVALID_ARG;
+    pdilqr_plan* pl = new (std::nothrow) pdilqr_plan();
+    if (!pl) return PDILQR_E_NO_MEMORY;
+    pdilqr_status st = plan_init(pl, b, o);
+    if (st != PDILQR_OK) {
+        delete pl;
+        return st;
+    }
+    *out = pl;
+    return PDILQR_OK;
+}
+
+extern "C" pdilqr_status pdilqr_plan_destroy(pdilqr_plan* pl)
+{
+    delete pl;
+    return PDILQR_OK;
+}
+
+extern "C" int32_t pdilqr_plan_warps(const pdilqr_plan* pl) { return pl ? pl->warps : 0; }
+
+// ------------------------------------------------------------- KKT solves
+static KktArgs make_args(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s, float* dx,
+                         float* du, float* dl, float* K, float* k, float* P, float* p,
+                         int32_t* status)
+{
+    KktArgs a;
+    a.A = lq->A; a.B = lq->B; a.c = lq->c; a.Q = lq->Q; a.R = lq->R; a.S = lq->S;
+    a.q = lq->q; a.r = lq->r;
+    a.s = s;
+    a.dx = dx; a.du = du; a.dlam = dl;
+    a.K = K ? K : pl->K;
+    a.k = k ? k : pl->k;
+    a.P = P ? P : pl->P;
+    a.p = p ? p : pl->p;
+    a.Abar = pl->Abar;
+    a.bbar = pl->bbar;
+    a.N = pl->dN;
+    a.off = pl->doff;
+    a.order = pl->dorder;
+    a.status = status;
+    a.count = pl->count;
+    return a;
+}
+
+static bool lq_ok(const pdilqr_lq* lq)
+{
+    return lq && lq->A && lq->B && lq->c && lq->Q && lq->R && lq->q && lq->r;
+}
+
+static pdilqr_status residual_into(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s,
+                                   const float* dx, const float* du, const float* dl,
+                                   double* norms, bool want_rhs, cudaStream_t st)
+{
+    PD_CUDA(cudaMemsetAsync(norms, 0, sizeof(double) * 4 * pl->count, st));
+    ResidArgs r;
+    r.A = lq->A; r.B = lq->B; r.c = lq->c; r.Q = lq->Q; r.R = lq->R; r.S = lq->S;
+    r.q = lq->q; r.r = lq->r; r.s = s;
+    r.dx = dx; r.du = du; r.dlam = dl;
+    r.N = pl->dN;
+    r.off = pl->doff;
+    r.stage_inst = pl->dstage_inst;
+    r.total_stages = pl->total;
+    r.norms = norms;
+    r.rq = want_rhs ? pl->rq : nullptr;
+    r.rr = want_rhs ? pl->rr : nullptr;
+    r.rc = want_rhs ? pl->rc : nullptr;
+    r.rs = want_rhs ? pl->rs : nullptr;
+    PD_CUDA(pl->ops->resid(r, st));
+    return PDILQR_OK;
+}
+
+static cudaError_t launch_axpy(float* z, const float* dz, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    axpy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(z, dz, n);
+    return cudaGetLastError();
+}
+
+static pdilqr_status solve_common(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s,
+                                  pdilqr_kkt_out* out, cudaStream_t st, bool scan)
+{
+    if (!pl || !lq_ok(lq) || !s || !out || !out->dx || !out->du || !out->dlam || !out->status)
+        return PDILQR_E_INVALID_ARG;
+    if (scan && !pl->ops->scan_ok) return PDILQR_E_INVALID_ARG;
+    auto run = [&](const KktArgs& a) -> cudaError_t {
+        return scan ? pl->ops->scan(a, pl->warps, st) : pl->ops->riccati(a, st);
+    };
+    KktArgs a = make_args(pl, lq, s, out->dx, out->du, out->dlam, out->K, out->k, out->P,
+                          out->p, out->status);
+    PD_CUDA(run(a));
+    if (pl->refine) {
+        // one correction solve against the FP64 residual
+        pdilqr_status rs = residual_into(pl, lq, s, out->dx, out->du, out->dlam, pl->norms,
+                                         true, st);
+        if (rs != PDILQR_OK) return rs;
+        pdilqr_lq corr = {lq->A, lq->B, pl->rc, lq->Q, lq->R, lq->S, pl->rq, pl->rr};
+        KktArgs b = make_args(pl, &corr, pl->rs, pl->ddx, pl->ddu, pl->ddl, nullptr, nullptr,
+                              nullptr, nullptr, pl->st2);
+        PD_CUDA(run(b));
+        const int64_t T = pl->total;
+        PD_CUDA(launch_axpy(out->dx, pl->ddx, T * pl->n, st));
+        PD_CUDA(launch_axpy(out->du, pl->ddu, T * pl->m, st));
+        PD_CUDA(launch_axpy(out->dlam, pl->ddl, T * pl->n, st));
+        if (out->k) PD_CUDA(launch_axpy(out->k, pl->k, T * pl->m, st));
+        if (out->p) PD_CUDA(launch_axpy(out->p, pl->p, T * pl->n, st));
+    }
+    if (out->resid) {
+        pdilqr_status rs = residual_into(pl, lq, s, out->dx, out->du, out->dlam, out->resid,
+                                         false, st);
+        if (rs != PDILQR_OK) return rs;
+    }
+    return PDILQR_OK;
+}
+
+extern "C" pdilqr_status pdilqr_kkt_scan_solve(pdilqr_plan* pl, const pdilqr_lq* lq,
+                                               const float* s, pdilqr_kkt_out* out,
+                                               pdilqr_stream stream)
+{
+    return solve_common(pl, lq, s, out, (cudaStream_t)stream, true);
+}
+
+extern "C" pdilqr_status pdilqr_riccati_solve(pdilqr_plan* pl, const pdilqr_lq* lq,
+                                              const float* s, pdilqr_kkt_out* out,
+                                              pdilqr_stream stream)
+{
+    return solve_common(pl, lq, s, out, (cudaStream_t)stream, false);
+}
+
+extern "C" pdilqr_status pdilqr_kkt_residual(pdilqr_plan* pl, const pdilqr_lq* lq,
+                                             const float* s, const float* dx, const float* du,
+                                             const float* dlam, double* resid,
+                                             pdilqr_stream stream)
+{
+    if (!pl || !lq_ok(lq) || !s || !dx || !du || !dlam || !resid) return PDILQR_E_INVALID_ARG;
+    return residual_into(pl, lq, s, dx, du, dlam, resid, false, (cudaStream_t)stream);
+}

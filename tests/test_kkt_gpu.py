@@ -1,0 +1,215 @@
+"""Parity of the GPU LQ KKT solvers (scan and sequential Riccati) with the
+FP64 oracle, through the C ABI.
+
+Tolerances (stated by the target): per block (dx, du, dlam) the relative
+error |z_gpu - z_ref|_inf / |z_ref|_inf <= 1e-4, and with the FP64-residual
+refinement step the normwise KKT backward error <= 1e-6.  The oracle solves
+the same FP32-rounded data in FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_07823_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+BWD_TOL = 1e-6
+
+
+def rounded(lq):
+    return {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in lq.items()}
+
+
+def lq_with_S(n, m, N, seed):
+    """Random convex LQ data with a nonzero cross term S."""
+    g = np.random.default_rng(seed)
+    d = synth.ltv_lq(n, m, N, seed, rho=0.95, b_std=0.5, q_kind="diag", r_w=0.1)
+    for k in range(N):
+        L = g.normal(0, 0.3, (n + m, n + m))
+        H = L @ L.T + 0.2 * np.eye(n + m)
+        d["Q"][k] = H[:n, :n]
+        d["R"][k] = H[n:, n:]
+        d["S"][k] = H[n:, :n]
+    return d
+
+
+def make_batch(n, m, Ns, seed, with_S=False, **kw):
+    insts = []
+    for i, N in enumerate(Ns):
+        if with_S:
+            insts.append(lq_with_S(n, m, N, seed + i))
+        else:
+            args = dict(rho=0.95, b_std=0.5, q_kind="diag", r_w=0.1)
+            args.update(kw)
+            insts.append(synth.ltv_lq(n, m, N, seed + i, **args))
+    packed, Nv, off = synth.pack(insts, synth.LQ_KEYS)
+    s = np.stack([inst["s"] for inst in insts])
+    return insts, packed, Nv, off, s
+
+
+def to_dev(packed, s, with_S):
+    lq = {k: torch.tensor(np.asarray(v, dtype=np.float32), device="cuda") for k, v in packed.items()}
+    if not with_S:
+        lq["S"] = None
+    return lq, torch.tensor(np.asarray(s, dtype=np.float32), device="cuda")
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+
+
+def check_parity(insts, Nv, off, out, s, with_S, policy=False):
+    dx = out["dx"].double().cpu().numpy()
+    du = out["du"].double().cpu().numpy()
+    dl = out["dlam"].double().cpu().numpy()
+    st = out["status"].cpu().numpy()
+    assert np.all(st == 0), st
+    worst = 0.0
+    for i, inst in enumerate(insts):
+        N, o = int(Nv[i]), int(off[i])
+        lq = rounded({k: inst[k] for k in synth.LQ_KEYS})
+        si = np.asarray(s[i], dtype=np.float32).astype(np.float64)
+        ref = oracle.riccati_solve(lq, si)
+        sl = slice(o, o + N + 1)
+        e = max(rel(dx[sl], ref["dx"]), rel(du[o:o + N], ref["du"][:N]), rel(dl[sl], ref["dlam"]))
+        worst = max(worst, e)
+        assert rel(dx[sl], ref["dx"]) <= REL_TOL, (i, N, rel(dx[sl], ref["dx"]))
+        assert rel(du[o:o + N], ref["du"][:N]) <= REL_TOL, (i, N)
+        assert rel(dl[sl], ref["dlam"]) <= REL_TOL, (i, N)
+        assert np.all(du[o + N] == 0.0)
+        if policy:
+            K = out["K"].double().cpu().numpy()[sl]
+            P = out["P"].double().cpu().numpy()[sl]
+            assert rel(K[:N], ref["K"][:N]) <= REL_TOL
+            assert rel(P, ref["P"]) <= REL_TOL
+    return worst
+
+
+@pytest.mark.parametrize("solver", ["scan", "riccati"])
+@pytest.mark.parametrize("warps", [4, 8, 16])
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (3, 2), (4, 2), (12, 12)])
+def test_ltv_parity_ragged(solver, warps, n, m):
+    """Uneven horizons in one batch: N = 1 (degenerate), tiny, and spanning
+    several chunks with a ragged tail."""
+    if solver == "riccati" and warps != 4:
+        pytest.skip("warp count only affects the scan")
+    Ns = [1, 2, 3, 5, 16, 17, 50, 100]
+    insts, packed, Nv, off, s = make_batch(n, m, Ns, seed=100 * n + m)
+    from paper_2506_07823_b300.pdilqr import Plan
+    plan = Plan(n, m, Nv, off, warps=warps)
+    lq, sd = to_dev(packed, s, False)
+    fn = plan.kkt_scan_solve if solver == "scan" else plan.riccati_solve
+    out = fn(lq, sd, want_policy=True)
+    torch.cuda.synchronize()
+    check_parity(insts, Nv, off, out, s, False, policy=True)
+
+
+@pytest.mark.parametrize("solver", ["scan", "riccati"])
+def test_cross_term_S(solver):
+    n, m = 4, 2
+    insts, packed, Nv, off, s = make_batch(n, m, [7, 30, 64], seed=5, with_S=True)
+    from paper_2506_07823_b300.pdilqr import Plan
+    plan = Plan(n, m, Nv, off, warps=8)
+    lq, sd = to_dev(packed, s, True)
+    fn = plan.kkt_scan_solve if solver == "scan" else plan.riccati_solve
+    out = fn(lq, sd)
+    torch.cuda.synchronize()
+    check_parity(insts, Nv, off, out, s, True)
+
+
+def test_single_lqr_workload_exact_config():
+    """The small single-LQR workload: n=4, m=2, N=16, seed 0."""
+    cfg = synth.LQ_SMALL
+    inst = synth.ltv_lq(cfg["n"], cfg["m"], cfg["N"], seed=0, rho=cfg["rho"], b_std=cfg["b_std"],
+                        q_kind=cfg["q_kind"], r_w=cfg["r_w"])
+    packed, Nv, off = synth.pack([inst], synth.LQ_KEYS)
+    from paper_2506_07823_b300.pdilqr import Plan, backward_error
+    plan = Plan(4, 2, Nv, off, refine=True)
+    lq, sd = to_dev(packed, inst["s"][None], False)
+    out = plan.kkt_scan_solve(lq, sd, want_resid=True)
+    torch.cuda.synchronize()
+    check_parity([inst], Nv, off, out, inst["s"][None], False)
+    assert float(backward_error(out["resid"]).max()) <= BWD_TOL
+
+
+@pytest.mark.parametrize("solver", ["scan", "riccati"])
+@pytest.mark.parametrize("n,m", [(4, 2), (12, 12)])
+def test_refinement_backward_error(solver, n, m):
+    """One refinement step against the FP64 residual brings the normwise
+    backward error to <= 1e-6 and keeps the parity."""
+    insts, packed, Nv, off, s = make_batch(n, m, [10, 50, 100, 33], seed=77)
+    from paper_2506_07823_b300.pdilqr import Plan, backward_error
+    plan0 = Plan(n, m, Nv, off, refine=False)
+    plan1 = Plan(n, m, Nv, off, refine=True)
+    lq, sd = to_dev(packed, s, False)
+    fn0 = plan0.kkt_scan_solve if solver == "scan" else plan0.riccati_solve
+    fn1 = plan1.kkt_scan_solve if solver == "scan" else plan1.riccati_solve
+    o0 = fn0(lq, sd, want_resid=True)
+    o1 = fn1(lq, sd, want_resid=True)
+    torch.cuda.synchronize()
+    b0 = backward_error(o0["resid"]).cpu().numpy()
+    b1 = backward_error(o1["resid"]).cpu().numpy()
+    assert np.all(b1 <= BWD_TOL), b1
+    assert np.all(b1 <= b0 * 1.01 + 1e-12), (b0, b1)
+    check_parity(insts, Nv, off, o1, s, False)
+
+
+def test_residual_kernel_matches_oracle():
+    """The FP64 residual kernel reproduces the oracle's residual norms."""
+    n, m = 4, 2
+    insts, packed, Nv, off, s = make_batch(n, m, [3, 9], seed=3)
+    from paper_2506_07823_b300.pdilqr import Plan
+    plan = Plan(n, m, Nv, off)
+    lq, sd = to_dev(packed, s, False)
+    g = np.random.default_rng(0)
+    T = plan.total
+    z = [g.normal(0, 1, (T, n)).astype(np.float32), g.normal(0, 1, (T, m)).astype(np.float32),
+         g.normal(0, 1, (T, n)).astype(np.float32)]
+    for i, N in enumerate(Nv):
+        z[1][off[i] + N] = 0.0
+    res = plan.kkt_residual(lq, sd, *[torch.tensor(v, device="cuda") for v in z])
+    torch.cuda.synchronize()
+    res = res.cpu().numpy()
+    for i, inst in enumerate(insts):
+        N, o = int(Nv[i]), int(off[i])
+        lqr = rounded({k: inst[k] for k in synth.LQ_KEYS})
+        want = oracle.kkt_residual(lqr, np.asarray(s[i], np.float32).astype(np.float64),
+                                   *[v[o:o + N + 1].astype(np.float64) for v in z])
+        np.testing.assert_allclose(res[i], want, rtol=1e-12)
+
+
+def test_not_spd_status():
+    """A control Hessian that is not positive definite is reported, not hidden."""
+    n, m = 4, 2
+    insts, packed, Nv, off, s = make_batch(n, m, [6, 6], seed=9)
+    packed["R"][off[1] + 2] = -np.eye(m)
+    from paper_2506_07823_b300.pdilqr import Plan
+    plan = Plan(n, m, Nv, off, warps=4)
+    lq, sd = to_dev(packed, s, False)
+    for fn in (plan.kkt_scan_solve, plan.riccati_solve):
+        out = fn(lq, sd)
+        torch.cuda.synchronize()
+        st = out["status"].cpu().numpy()
+        assert st[0] == 0 and st[1] != 0
+
+
+def test_batch_alone_equals_in_mix():
+    """An instance solved alone equals the same instance inside a batch."""
+    n, m = 12, 12
+    insts, packed, Nv, off, s = make_batch(n, m, [40, 25, 75, 100, 1], seed=31)
+    from paper_2506_07823_b300.pdilqr import Plan
+    plan = Plan(n, m, Nv, off, warps=8)
+    lq, sd = to_dev(packed, s, False)
+    mix = plan.kkt_scan_solve(lq, sd)
+    i = 2
+    pk1, Nv1, off1 = synth.pack([insts[i]], synth.LQ_KEYS)
+    plan1 = Plan(n, m, Nv1, off1, warps=8)
+    lq1, sd1 = to_dev(pk1, s[i:i + 1], False)
+    alone = plan1.kkt_scan_solve(lq1, sd1)
+    torch.cuda.synchronize()
+    sl = slice(int(off[i]), int(off[i]) + int(Nv[i]) + 1)
+    assert torch.equal(mix["dx"][sl], alone["dx"])
+    assert torch.equal(mix["dlam"][sl], alone["dlam"])
