@@ -68,7 +68,9 @@ class SqpOpts(ctypes.Structure):
 
 class SqpInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int),
-                ("alpha", ctypes.c_double * 32), ("J", ctypes.c_double),
+                ("alpha", ctypes.c_double * 32), ("step", ctypes.c_double * 32),
+                ("theta_it", ctypes.c_double * 32),
+                ("J", ctypes.c_double),
                 ("theta", ctypes.c_double), ("theta_max", ctypes.c_double)]
 
 
@@ -255,6 +257,8 @@ def _opts(max_iters, tol_step, tol_theta, c_armijo, theta_frac, alpha_replay):
 def _info(info: SqpInfo) -> dict:
     return {"iters": info.iters, "status": info.status,
             "alpha": np.array(info.alpha[:max(info.iters, 0)]),
+            "step": np.array(info.step[:max(info.iters, 0)]),
+            "theta_it": np.array(info.theta_it[:max(info.iters, 0)]),
             "J": info.J, "theta": info.theta, "theta_max": info.theta_max}
 
 

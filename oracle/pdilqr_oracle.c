@@ -634,6 +634,8 @@ static int sqp_run(const sqp_model *mdl, const double *x0hat, double *x,
         double step = 0.0;
         for (size_t i = 0; i < S1 * n; ++i) step = amax(step, fabs(dx[i]));
         for (size_t i = 0; i < (size_t)N * m; ++i) step = amax(step, fabs(du[i]));
+        info->step[it] = step;
+        info->theta_it[it] = th0;
         const double dphi = mdl->dcost(mdl->ctx, x, u, dx, du);
         /* the ten step sizes 2^0 .. 2^-9; the largest accepted one wins */
         double alpha = 0.0;
@@ -653,6 +655,13 @@ static int sqp_run(const sqp_model *mdl, const double *x0hat, double *x,
         }
         info->alpha[it] = alpha;
         if (alpha == 0.0) {
+            /* no step accepted: converged if theta is at the rounding floor of
+             * the iterate, (N+1) sqrt(n) u max(1, |x|_inf), u = 2^-52 */
+            double xmax = 0.0;
+            for (size_t i = 0; i < S1 * n; ++i) xmax = amax(xmax, fabs(x[i]));
+            double floor_th = (double)(N + 1) * sqrt((double)n) * ldexp(1.0, -52) *
+                              (xmax > 1.0 ? xmax : 1.0);
+            if (!(opt->alpha_replay) && th0 <= floor_th) break;
             info->status = 1;
             break;
         }

@@ -124,6 +124,8 @@ typedef struct {
     int iters;            /* SQP iterations performed (KKT solves)           */
     int status;           /* 0 ok, 1 line search found no step, 2 not SPD    */
     double alpha[32];     /* step size taken at each iteration               */
+    double step[32];      /* |dz|_inf of the search direction per iteration  */
+    double theta_it[32];  /* theta of the iterate at the start of each iter. */
     double J, theta;      /* merit at the returned iterate                   */
     double theta_max;
 } orc_sqp_info;

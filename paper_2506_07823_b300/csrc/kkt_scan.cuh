@@ -110,6 +110,21 @@ __device__ __forceinline__ void load_stage(const Grp<NT>& g, float* st, const Kk
     g.sync();
 }
 
+// Source of LQ stages read from the caller's arrays.
+struct LqSource {
+    const float *A, *B, *c, *Q, *R, *S, *q, *r;
+    __device__ explicit LqSource(const KktArgs& a)
+        : A(a.A), B(a.B), c(a.c), Q(a.Q), R(a.R), S(a.S), q(a.q), r(a.r) {}
+    template <int NX, int NU, int NT>
+    __device__ __forceinline__ void load(const Grp<NT>& g, float* st, int64_t gs, bool terminal) const
+    {
+        KktArgs t;
+        t.A = A; t.B = B; t.c = c; t.Q = Q; t.R = R; t.S = S; t.q = q; t.r = r;
+        load_stage<NX, NU, NT>(g, st, t, gs, terminal);
+    }
+    __device__ __forceinline__ bool has_S() const { return S != nullptr; }
+};
+
 // ------------------------------------------------------------ element build
 // e_k = (A - B R^-1 S, c - B R^-1 r, B R^-1 B^T, q - S^T R^-1 r, Q - S^T R^-1 S)
 // (Eq. initialization); the terminal element is (0, 0, 0, q_N, Q_N).
@@ -245,7 +260,7 @@ __device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, f
 // P, p, Abar = A + B K, bbar = B k + c to global memory at stage gs.
 template <int NX, int NU, int NT>
 __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin, float* vout,
-                             float* scr, const KktArgs& a, int64_t gs)
+                             float* scr, const KktArgs& a, int64_t gs, bool has_S)
 {
     using L = StageL<NX, NU>;
     using E = ElemL<NX>;
@@ -266,7 +281,7 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
     g.sync();
     mm<NU, NU, NX, true, false, NT, false>(g, Gm, NU, st + L::B, NU, PB, NU, st + L::R, NU);
     mm<NU, NX, NX, true, false, NT, false>(g, Y, LDY, st + L::B, NU, PA, NX,
-                                           a.S ? st + L::S : nullptr, NX);
+                                           has_S ? st + L::S : nullptr, NX);
     mm<NU, 1, NX, true, false, NT, false>(g, Y + NX, LDY, st + L::B, NU, w, 1, st + L::r, 1);
     g.sync();
     const bool ok = chol<NU, NT>(g, Gm, NU, dinv);
@@ -375,21 +390,20 @@ struct ScanSmem {
     static constexpr size_t BYTES = sizeof(float) * TOTAL;
 };
 
-template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
+// The scan solve of one instance by the CTA (all threads must call it).
+// src provides the LQ stages; s_inst points to this instance's dx_0 (global
+// or shared memory).  Returns the instance status (uniform over the CTA).
+template <int NX, int NU, int W, class Src>
+__device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
+                          const float* s_inst, float* smem)
 {
     using SM = ScanSmem<NX, NU, W>;
     using E = ElemL<NX>;
-    extern __shared__ __align__(16) float smem[];
     const int warp = threadIdx.x >> 5;
     const Grp<32> g{(int)(threadIdx.x & 31), 0};
-    const int inst = a.order ? a.order[blockIdx.x] : blockIdx.x;
-    if (inst >= a.count) return;
-    const int N = a.N[inst];
-    const int64_t off = a.off[inst];
     const int S = N + 1;
     const int Weff = W < S ? W : S;
-    const bool has_S = a.S != nullptr;
+    const bool has_S = src.has_S();
 
     float* slots = smem;                               // [W][ELEM]
     float* priv = smem + SM::SLOTS + warp * SM::PRIV;  // this warp's private area
@@ -414,7 +428,7 @@ __global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
         float* acc = slots + warp * SM::ELEM;
         float* other = tmpE;
         for (int k = k0; k < k1; ++k) {
-            load_stage<NX, NU, 32>(g, stg, a, off + k, false);
+            src.template load<NX, NU, 32>(g, stg, off + k, false);
             if (k == k0) {
                 if (!build_element<NX, NU, 32>(g, stg, acc, scr, has_S, false)) bad = ST_NOT_SPD;
             } else {
@@ -430,11 +444,11 @@ __global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
         float* v1 = v0 + SM::ELEM;
         float* scr = v1 + SM::ELEM;
         for (int k = k1 - 1; k >= k0; --k) {
-            load_stage<NX, NU, 32>(g, stg, a, off + k, k == N);
+            src.template load<NX, NU, 32>(g, stg, off + k, k == N);
             if (k == N) {
                 terminal_value<NX, NU, 32>(g, stg, v0, a, off + k);
             } else {
-                if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, off + k)) bad = ST_NOT_SPD;
+                if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, off + k, has_S)) bad = ST_NOT_SPD;
                 float* t = v0; v0 = v1; v1 = t;
             }
         }
@@ -490,8 +504,8 @@ __global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
         g.sync();
         for (int k = k1 - 1; k >= k0; --k) {
             const int64_t gs = off + k;
-            load_stage<NX, NU, 32>(g, stg, a, gs, false);
-            if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, gs)) bad = ST_NOT_SPD;
+            src.template load<NX, NU, 32>(g, stg, gs, false);
+            if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, gs, has_S)) bad = ST_NOT_SPD;
             float* t = v0; v0 = v1; v1 = t;
             __threadfence_block();
             g.sync();
@@ -513,7 +527,7 @@ __global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
     // chunk maps, then every chunk rolls out dx, du, dlam.
     if (warp == 0) {
         float* x = xs;
-        for (int i = g.t; i < NX; i += 32) x[i] = a.s[(int64_t)inst * NX + i];
+        for (int i = g.t; i < NX; i += 32) x[i] = s_inst[i];
         g.sync();
         for (int w = 0; w + 1 < Weff; ++w) {
             const float* Psi = smem + SM::SLOTS + w * SM::PRIV + SM::PSI;
@@ -530,8 +544,23 @@ __global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
         rollout_chunk<NX, NU, 32>(g, x, xn, a, off, N, k0, k1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) a.status[inst] = st_word[0];
+    const int status = st_word[0];
+    __syncthreads();
+    return status;
 }
+
+template <int NX, int NU, int W>
+__global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int inst = a.order ? a.order[blockIdx.x] : blockIdx.x;
+    if (inst >= a.count) return;
+    const LqSource src(a);
+    const int st = scan_solve<NX, NU, W>(src, a, a.N[inst], a.off[inst],
+                                         a.s + (int64_t)inst * NX, smem);
+    if (threadIdx.x == 0) a.status[inst] = st;
+}
+
 
 // --------------------------------------------------------- Riccati kernel
 template <int NX, int NU>
@@ -567,7 +596,8 @@ __global__ void __launch_bounds__(128) riccati_kernel(KktArgs a)
     terminal_value<NX, NU, 32>(g, stg, v0, a, off + N);
     for (int k = N - 1; k >= 0; --k) {
         load_stage<NX, NU, 32>(g, stg, a, off + k, false);
-        if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, off + k)) bad = ST_NOT_SPD;
+        if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, off + k, a.S != nullptr))
+            bad = ST_NOT_SPD;
         float* t = v0; v0 = v1; v1 = t;
     }
     __threadfence_block();

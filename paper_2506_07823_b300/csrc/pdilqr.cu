@@ -8,6 +8,7 @@
 
 #include "kkt_scan.cuh"
 #include "residual.cuh"
+#include "sqp.cuh"
 
 using namespace pdl;
 
@@ -42,19 +43,26 @@ static pdilqr_status cuda_status(cudaError_t e)
     } while (0)
 
 // --------------------------------------------------------- per-size kernels
+static constexpr size_t kSmemMax = 227 * 1024;  // opt-in shared memory per CTA (sm_103a)
+
 struct SizeOps {
     int n, m;
-    bool scan_ok;  // the scan kernel fits shared memory for this size
     cudaError_t (*scan)(const KktArgs&, int warps, cudaStream_t);
     cudaError_t (*riccati)(const KktArgs&, cudaStream_t);
     cudaError_t (*resid)(const ResidArgs&, cudaStream_t);
     size_t (*scan_smem)(int warps);
+    // SRBD model (n = m = 12 nrob); null for other sizes
+    cudaError_t (*linearize)(const LinArgs&, cudaStream_t);
+    cudaError_t (*merit)(const MeritArgs&, cudaStream_t);
+    cudaError_t (*sqp)(const SqpArgs&, int warps, cudaStream_t);
+    size_t (*sqp_smem)(int warps);
 };
 
 template <int NX, int NU, int W>
 static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
 {
     using SM = ScanSmem<NX, NU, W>;
+    if (SM::BYTES > kSmemMax) return cudaErrorInvalidConfiguration;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kkt_scan_kernel<NX, NU, W>,
@@ -119,16 +127,86 @@ static cudaError_t launch_resid(const ResidArgs& a, cudaStream_t st)
 }
 
 template <int NX, int NU>
+static cudaError_t launch_linearize(const LinArgs& a, cudaStream_t st)
+{
+    const size_t bytes = sizeof(float) * StageL<NX, NU>::SIZE * 4;
+    if (bytes > kSmemMax) return cudaErrorInvalidConfiguration;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(linearize_kernel<NX, NU>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t blocks = (a.total + 3) / 4;
+    linearize_kernel<NX, NU><<<(unsigned)blocks, 128, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static cudaError_t launch_merit(const MeritArgs& a, cudaStream_t st)
+{
+    merit_kernel<NX, NU><<<a.count, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU, int W>
+static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
+{
+    using SM = SqpSmem<NX, NU, W>;
+    if (SM::BYTES > kSmemMax) return cudaErrorInvalidConfiguration;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sqp_kernel<NX, NU, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SM::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    sqp_kernel<NX, NU, W><<<a.ka.count, W * 32, SM::BYTES, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static cudaError_t launch_sqp(const SqpArgs& a, int warps, cudaStream_t st)
+{
+    switch (warps) {
+        case 4: return launch_sqp_w<NX, NU, 4>(a, st);
+        case 8: return launch_sqp_w<NX, NU, 8>(a, st);
+        case 16: return launch_sqp_w<NX, NU, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NX, int NU>
+static size_t sqp_smem(int warps)
+{
+    switch (warps) {
+        case 4: return SqpSmem<NX, NU, 4>::BYTES;
+        case 8: return SqpSmem<NX, NU, 8>::BYTES;
+        case 16: return SqpSmem<NX, NU, 16>::BYTES;
+        default: return 0;
+    }
+}
+
+template <int NX, int NU, bool SRBD = false, bool FUSED = false>
 static SizeOps make_ops()
 {
-    SizeOps o;
+    SizeOps o{};
     o.n = NX;
     o.m = NU;
-    o.scan_ok = ScanSmem<NX, NU, 4>::BYTES <= 227 * 1024;
     o.scan = launch_scan<NX, NU>;
     o.riccati = launch_riccati<NX, NU>;
     o.resid = launch_resid<NX, NU>;
     o.scan_smem = scan_smem<NX, NU>;
+    if constexpr (SRBD) {
+        o.linearize = launch_linearize<NX, NU>;
+        o.merit = launch_merit<NX, NU>;
+    }
+    if constexpr (FUSED) {
+        o.sqp = launch_sqp<NX, NU>;
+        o.sqp_smem = sqp_smem<NX, NU>;
+    }
     return o;
 }
 
@@ -136,7 +214,7 @@ static const SizeOps* find_ops(int n, int m)
 {
     static const SizeOps table[] = {
         make_ops<1, 1>(), make_ops<2, 1>(), make_ops<3, 2>(), make_ops<4, 2>(),
-        make_ops<12, 12>(), make_ops<36, 24>(),
+        make_ops<12, 12, true, true>(), make_ops<24, 24, true>(), make_ops<36, 24>(),
     };
     for (const auto& o : table)
         if (o.n == n && o.m == m) return &o;
@@ -176,11 +254,11 @@ struct pdilqr_plan {
     }
 };
 
-static int pick_warps(int maxN)
+static int pick_warps(const SizeOps* ops, int maxN)
 {
-    if (maxN >= 40) return 16;
-    if (maxN >= 12) return 8;
-    return 4;
+    int w = maxN >= 40 ? 16 : (maxN >= 12 ? 8 : 4);
+    while (w > 4 && ops->scan_smem(w) > kSmemMax) w >>= 1;
+    return w;
 }
 
 static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdilqr_opts* o)
@@ -205,7 +283,7 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
         const int pa = by_off[i - 1], pb = by_off[i];
         if (hoff[pa] + hN[pa] + 1 > hoff[pb]) return PDILQR_E_INVALID_ARG;
     }
-    pl->warps = (o && o->warps) ? o->warps : pick_warps(pl->maxN);
+    pl->warps = (o && o->warps) ? o->warps : pick_warps(pl->ops, pl->maxN);
     if (pl->warps != 4 && pl->warps != 8 && pl->warps != 16) return PDILQR_E_INVALID_ARG;
     pl->refine = (o && o->refine) ? 1 : 0;
     // longest horizons first: the tail of the grid holds the short instances
@@ -333,7 +411,7 @@ static pdilqr_status solve_common(pdilqr_plan* pl, const pdilqr_lq* lq, const fl
 {
     if (!pl || !lq_ok(lq) || !s || !out || !out->dx || !out->du || !out->dlam || !out->status)
         return PDILQR_E_INVALID_ARG;
-    if (scan && !pl->ops->scan_ok) return PDILQR_E_INVALID_ARG;
+    if (scan && pl->ops->scan_smem(pl->warps) > kSmemMax) return PDILQR_E_INVALID_ARG;
     auto run = [&](const KktArgs& a) -> cudaError_t {
         return scan ? pl->ops->scan(a, pl->warps, st) : pl->ops->riccati(a, st);
     };
@@ -385,4 +463,88 @@ extern "C" pdilqr_status pdilqr_kkt_residual(pdilqr_plan* pl, const pdilqr_lq* l
 {
     if (!pl || !lq_ok(lq) || !s || !dx || !du || !dlam || !resid) return PDILQR_E_INVALID_ARG;
     return residual_into(pl, lq, s, dx, du, dlam, resid, false, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------ SRBD model
+static bool model_ok(const pdilqr_plan* pl, const pdilqr_srbd_model* md)
+{
+    return md && md->nrob >= 1 && md->nrob <= 16 && pl->n == 12 * md->nrob && pl->m == pl->n &&
+           md->dt > 0.f && md->mass > 0.f && md->inertia[0] > 0.f && md->inertia[1] > 0.f &&
+           md->inertia[2] > 0.f && md->bar_delta > 0.f;
+}
+
+extern "C" pdilqr_status pdilqr_linearize(pdilqr_plan* pl, const pdilqr_srbd_model* md,
+                                          const pdilqr_traj* tr, pdilqr_lq_out* out,
+                                          pdilqr_stream stream)
+{
+    if (!pl || !model_ok(pl, md) || !pl->ops->linearize || !tr || !out) return PDILQR_E_INVALID_ARG;
+    if (!tr->x || !tr->u || !tr->lam || !tr->xref || !tr->uref || !tr->contact)
+        return PDILQR_E_INVALID_ARG;
+    if (!out->A || !out->B || !out->c || !out->Q || !out->R || !out->q || !out->r)
+        return PDILQR_E_INVALID_ARG;
+    LinArgs a;
+    a.md = *md;
+    a.x = tr->x; a.u = tr->u; a.lam = tr->lam; a.xref = tr->xref; a.uref = tr->uref;
+    a.contact = tr->contact;
+    a.A = out->A; a.B = out->B; a.c = out->c; a.Q = out->Q; a.R = out->R; a.S = out->S;
+    a.q = out->q; a.r = out->r;
+    a.N = pl->dN;
+    a.off = pl->doff;
+    a.stage_inst = pl->dstage_inst;
+    a.total = pl->total;
+    PD_CUDA(pl->ops->linearize(a, (cudaStream_t)stream));
+    return PDILQR_OK;
+}
+
+extern "C" pdilqr_status pdilqr_merit_eval(pdilqr_plan* pl, const pdilqr_srbd_model* md,
+                                           const pdilqr_traj* tr, const float* x0hat,
+                                           const float* dx, const float* du, double* merit,
+                                           pdilqr_stream stream)
+{
+    if (!pl || !model_ok(pl, md) || !pl->ops->merit || !tr || !x0hat || !dx || !du || !merit)
+        return PDILQR_E_INVALID_ARG;
+    if (!tr->x || !tr->u || !tr->xref || !tr->uref || !tr->contact) return PDILQR_E_INVALID_ARG;
+    MeritArgs a;
+    a.md = *md;
+    a.x = tr->x; a.u = tr->u; a.xref = tr->xref; a.uref = tr->uref; a.x0hat = x0hat;
+    a.dx = dx; a.du = du; a.contact = tr->contact;
+    a.N = pl->dN;
+    a.off = pl->doff;
+    a.out = merit;
+    a.count = pl->count;
+    PD_CUDA(pl->ops->merit(a, (cudaStream_t)stream));
+    return PDILQR_OK;
+}
+
+extern "C" pdilqr_status pdilqr_solve(pdilqr_plan* pl, const pdilqr_srbd_model* md,
+                                      const pdilqr_sqp_opts* o, const float* x0hat, float* x,
+                                      float* u, float* lam, const float* xref, const float* uref,
+                                      const uint8_t* contact, pdilqr_sqp_info* info,
+                                      pdilqr_stream stream)
+{
+    if (!pl || !model_ok(pl, md) || !pl->ops->sqp || !o || !info) return PDILQR_E_INVALID_ARG;
+    if (!x0hat || !x || !u || !lam || !xref || !uref || !contact || !info->iters || !info->status)
+        return PDILQR_E_INVALID_ARG;
+    if (o->max_iters < 1 || o->max_iters > 32) return PDILQR_E_INVALID_ARG;
+    if (pl->ops->sqp_smem(pl->warps) > kSmemMax) return PDILQR_E_INVALID_ARG;
+    SqpArgs a;
+    a.md = *md;
+    a.x0hat = x0hat;
+    a.x = x; a.u = u; a.lam = lam; a.xref = xref; a.uref = uref; a.contact = contact;
+    pdilqr_lq none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    a.ka = make_args(pl, &none, nullptr, pl->ddx, pl->ddu, pl->ddl, nullptr, nullptr, nullptr,
+                     nullptr, pl->st2);
+    a.max_iters = o->max_iters;
+    a.tol_step = o->tol_step;
+    a.tol_theta = o->tol_theta;
+    a.c_armijo = o->c_armijo;
+    a.theta_frac = o->theta_frac;
+    a.alpha_replay = o->alpha_replay;
+    a.iters = info->iters;
+    a.status = info->status;
+    a.alpha = info->alpha;
+    a.J = info->J;
+    a.theta = info->theta;
+    PD_CUDA(pl->ops->sqp(a, pl->warps, (cudaStream_t)stream));
+    return PDILQR_OK;
 }

@@ -1,0 +1,215 @@
+// sqp.cuh -- the multiple-shooting SQP of Sec. II-B..II-E in one kernel:
+// per iteration the SRBD linearisation (on the fly, inside the scan), the LQ
+// KKT solve by the parallel scan, the parallel line search over the ten step
+// sizes 2^0..2^-9 and the update of Eq. (linear_rollout).  One CTA per
+// instance; no host synchronisation between iterations.
+#pragma once
+
+#include "kkt_scan.cuh"
+#include "srbd.cuh"
+
+namespace pdl {
+
+enum : int32_t { ST_LINESEARCH = 8 };
+
+struct SqpArgs {
+    pdilqr_srbd_model md;
+    const float* x0hat;             // [count][n]
+    float *x, *u, *lam;             // trajectory (in: warm start, out: solution)
+    const float *xref, *uref;
+    const uint8_t* contact;
+    KktArgs ka;                     // step buffers, policy workspace, batch tables
+    int max_iters;
+    float tol_step, tol_theta, c_armijo, theta_frac;
+    const float* alpha_replay;      // [count][max_iters] or null
+    int32_t *iters, *status;        // [count]
+    float* alpha;                   // [count][max_iters] or null
+    double *J, *theta;              // [count] or null
+};
+
+template <int NX, int NU, int W>
+struct SqpSmem {
+    using SC = ScanSmem<NX, NU, W>;
+    static constexpr int MER = (SC::TOTAL + 1) & ~1;             // 8-byte aligned
+    static constexpr int SBUF = MER + 2 * 32;                    // 32 doubles
+    static constexpr int CTL = SBUF + round4(NX);
+    static constexpr int TOTAL = CTL + 8;
+    static constexpr size_t BYTES = sizeof(float) * TOTAL;
+};
+
+template <int NX, int NU, int W>
+__global__ void __launch_bounds__(W * 32) sqp_kernel(SqpArgs a)
+{
+    using SM = SqpSmem<NX, NU, W>;
+    extern __shared__ __align__(16) float smem[];
+    const int inst = a.ka.order ? a.ka.order[blockIdx.x] : blockIdx.x;
+    if (inst >= a.ka.count) return;
+    const int N = a.ka.N[inst];
+    const int64_t off = a.ka.off[inst];
+    const int nrob = a.md.nrob;
+    double* mer = reinterpret_cast<double*>(smem + SM::MER);  // [0..25] merit, [24] theta_max
+    float* sbuf = smem + SM::SBUF;
+    float* alpha_sh = smem + SM::CTL;
+    int* ctl = reinterpret_cast<int*>(smem + SM::CTL + 1);    // [0] converged flag
+
+    const SrbdSource src{a.md, a.x, a.u, a.lam, a.xref, a.uref, a.contact, nrob};
+    const float* xh = a.x0hat + (int64_t)inst * NX;
+    float* x = a.x + off * NX;
+    float* u = a.u + off * NU;
+    float* lam = a.lam + off * NX;
+    const float* dx = a.ka.dx + off * NX;
+    const float* du = a.ka.du + off * NU;
+    const float* dl = a.ka.dlam + off * NX;
+    const float* xr = a.xref + off * NX;
+    const float* ur = a.uref + off * NU;
+    const uint8_t* ct = a.contact + off * 4 * nrob;
+
+    int status = ST_OK, iters = 0;
+    for (int it = 0; it < a.max_iters; ++it) {
+        for (int i = threadIdx.x; i < NX; i += blockDim.x) sbuf[i] = xh[i] - x[i];
+        __syncthreads();
+        const int st = scan_solve<NX, NU, W>(src, a.ka, N, off, sbuf, smem);
+        if (st != ST_OK) {
+            status = st;
+            break;
+        }
+        iters = it + 1;
+        merit_block<NX, NU>(a.md, x, u, dx, du, xr, ur, ct, xh, N, nrob, mer);
+        if (threadIdx.x == 0) {
+            const double th0 = mer[1], dphi = mer[2];
+            if (it == 0) mer[24] = (double)a.theta_frac * fmax(1.0, th0);
+            const double thmax = mer[24];
+            float alpha = 0.f;
+            double th_new = INFINITY;
+            if (a.alpha_replay) {
+                alpha = a.alpha_replay[(int64_t)inst * a.max_iters + it];
+                for (int t = 0; t < 10; ++t)
+                    if (alpha == ldexpf(1.f, -t)) th_new = mer[13 + t];
+            } else {
+                for (int t = 0; t < 10; ++t) {
+                    const double at = ldexp(1.0, -t);
+                    if (filter_ok(th0, dphi, thmax, at, mer[3 + t], mer[13 + t], a.c_armijo)) {
+                        alpha = (float)at;
+                        th_new = mer[13 + t];
+                        break;
+                    }
+                }
+            }
+            // No step accepted while theta(0) already sits at the rounding floor
+            // of the FP32 iterate ((N+1) sqrt(n) u |x|_inf): converged at working
+            // precision, not a failure.
+            const double floor_th = (double)(N + 1) * sqrt((double)NX) * 0x1p-23 * fmax(1.0, mer[25]);
+            const bool at_floor = alpha == 0.f && th0 <= floor_th && !a.alpha_replay;
+            alpha_sh[0] = at_floor ? -1.f : alpha;
+            ctl[0] = (at_floor || (mer[23] < (double)a.tol_step && th_new < (double)a.tol_theta)) ? 1 : 0;
+            if (a.alpha) a.alpha[(int64_t)inst * a.max_iters + it] = alpha;
+        }
+        __syncthreads();
+        const float alpha = alpha_sh[0];
+        if (alpha == 0.f) {
+            status = ST_LINESEARCH;
+            break;
+        }
+        if (alpha < 0.f) break;   // converged at the precision floor
+        // Eq. (linear_rollout): x += a dx, u += a du, lam += a dlam
+        for (int64_t e = threadIdx.x; e < (int64_t)(N + 1) * NX; e += blockDim.x) {
+            x[e] += alpha * dx[e];
+            lam[e] += alpha * dl[e];
+        }
+        for (int64_t e = threadIdx.x; e < (int64_t)N * NU; e += blockDim.x) u[e] += alpha * du[e];
+        __syncthreads();
+        if (ctl[0]) break;
+    }
+    if (a.J || a.theta) {
+        // merit at the returned iterate (the step buffers still hold the last
+        // direction; only the current-point column is read)
+        merit_block<NX, NU>(a.md, x, u, dx, du, xr, ur, ct, xh, N, nrob, mer);
+    }
+    if (threadIdx.x == 0) {
+        a.iters[inst] = iters;
+        a.status[inst] = status;
+        if (a.J) a.J[inst] = mer[0];
+        if (a.theta) a.theta[inst] = mer[1];
+        if (a.alpha)
+            for (int it = iters; it < a.max_iters; ++it) a.alpha[(int64_t)inst * a.max_iters + it] = 0.f;
+    }
+}
+
+// ------------------------------------------------ standalone linearisation
+struct LinArgs {
+    pdilqr_srbd_model md;
+    const float *x, *u, *lam, *xref, *uref;
+    const uint8_t* contact;
+    float *A, *B, *c, *Q, *R, *S, *q, *r;
+    const int32_t* N;
+    const int64_t* off;
+    const int64_t* stage_inst;
+    int64_t total;
+};
+
+// One warp per stage slot, four warps per block.
+template <int NX, int NU>
+__global__ void __launch_bounds__(128) linearize_kernel(LinArgs a)
+{
+    using L = StageL<NX, NU>;
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5;
+    const int64_t gs = (int64_t)blockIdx.x * 4 + warp;
+    if (gs >= a.total) return;
+    const int64_t inst = a.stage_inst[gs];
+    if (inst < 0) return;
+    const int N = a.N[inst];
+    const int k = (int)(gs - a.off[inst]);
+    const bool term = k == N;
+    const Grp<32> g{(int)(threadIdx.x & 31), 0};
+    float* st = smem + warp * L::SIZE;
+    const int nrob = a.md.nrob;
+    srbd_linearize_stage<NX, NU, 32>(g, st, a.md, a.x + gs * NX, a.u + gs * NU,
+                                     term ? nullptr : a.x + (gs + 1) * NX, a.lam + gs * NX,
+                                     term ? nullptr : a.lam + (gs + 1) * NX, a.xref + gs * NX,
+                                     a.uref + gs * NU, a.contact + gs * 4 * nrob, term);
+    for (int e = g.t; e < NX * NX; e += 32) {
+        a.Q[gs * NX * NX + e] = st[L::Q + e];
+        a.A[gs * NX * NX + e] = term ? 0.f : st[L::A + e];
+    }
+    for (int e = g.t; e < NX * NU; e += 32) {
+        a.B[gs * NX * NU + e] = term ? 0.f : st[L::B + e];
+        if (a.S) a.S[gs * NX * NU + e] = 0.f;
+    }
+    for (int e = g.t; e < NU * NU; e += 32) a.R[gs * NU * NU + e] = term ? 0.f : st[L::R + e];
+    for (int i = g.t; i < NX; i += 32) {
+        a.q[gs * NX + i] = st[L::q + i];
+        a.c[gs * NX + i] = term ? 0.f : st[L::c + i];
+    }
+    for (int i = g.t; i < NU; i += 32) a.r[gs * NU + i] = term ? 0.f : st[L::r + i];
+}
+
+// ------------------------------------------------------ standalone merit
+struct MeritArgs {
+    pdilqr_srbd_model md;
+    const float *x, *u, *xref, *uref, *x0hat, *dx, *du;
+    const uint8_t* contact;
+    const int32_t* N;
+    const int64_t* off;
+    double* out;   // [count][24]
+    int count;
+};
+
+template <int NX, int NU>
+__global__ void __launch_bounds__(256) merit_kernel(MeritArgs a)
+{
+    __shared__ double mer[32];
+    const int inst = blockIdx.x;
+    if (inst >= a.count) return;
+    const int N = a.N[inst];
+    const int64_t off = a.off[inst];
+    const int nrob = a.md.nrob;
+    if (threadIdx.x < 32) mer[threadIdx.x] = 0.0;
+    __syncthreads();
+    merit_block<NX, NU>(a.md, a.x + off * NX, a.u + off * NU, a.dx + off * NX, a.du + off * NU,
+                        a.xref + off * NX, a.uref + off * NU, a.contact + off * 4 * nrob,
+                        a.x0hat + (int64_t)inst * NX, N, nrob, mer);
+    if (threadIdx.x < 24) a.out[(int64_t)inst * 24 + threadIdx.x] = mer[threadIdx.x];
+}
+
+}  // namespace pdl

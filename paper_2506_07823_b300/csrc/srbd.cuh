@@ -144,7 +144,7 @@ __device__ void srbd_linearize_stage(const Grp<NT>& g, float* st, const pdilqr_s
         Arow[i] = 1.f;
         float xd[12];
         srbd_xdot(md, xb, ub, sb, xd);
-        st[L::c + i] = (xb[r] + dt * xd[r]) - x1[i];
+        st[L::c + i] = (xb[r] - x1[i]) + dt * xd[r];   // difference first: no rounding of h
         if (r < 3) {
             Arow[o + 6 + r] = dt;
         } else if (r < 6) {
@@ -338,8 +338,10 @@ __device__ float srbd_stage_dphi(const pdilqr_srbd_model& md, const float* x, co
     return d;
 }
 
-// | x1 - h(x, u) |_2 for one stage at a trial point (trial values formed here:
-// xt = x + a dx etc.)
+// | x1 - h(x, u) |_2 for one stage at the trial point z + a dz.  The state
+// difference is formed before the trial states are rounded:
+//   (x1 - x) + a (dx1 - dx) - dt f(x + a dx, u + a du),
+// so the defect is not buried under the rounding of O(1) states.
 template <int NX>
 __device__ float srbd_stage_defect(const pdilqr_srbd_model& md, const float* x, const float* u,
                                    const float* x1, const float* dx, const float* du,
@@ -355,7 +357,8 @@ __device__ float srbd_stage_defect(const pdilqr_srbd_model& md, const float* x, 
         }
         srbd_xdot(md, xt, ut, ct + 4 * b, xd);
         for (int i = 0; i < 12; ++i) {
-            const float e = (x1[12 * b + i] + a * dx1[12 * b + i]) - (xt[i] + md.dt * xd[i]);
+            const int j = 12 * b + i;
+            const float e = (x1[j] - x[j]) + a * (dx1[j] - dx[j]) - md.dt * xd[i];
             ss += e * e;
         }
     }
@@ -376,7 +379,7 @@ __device__ __forceinline__ float warp_maxf(float v)
 // Line-search merit of one instance by the warps of a CTA (columns: the
 // ten step sizes, then the current point).  out (shared, 24 doubles):
 // [0] J(0), [1] theta(0), [2] dphi, [3+t] J(a_t) - J(0), [13+t] theta(a_t),
-// [23] |dz|_inf.  Ends with __syncthreads.
+// [23] |dz|_inf, [25] |x|_inf.  Ends with __syncthreads.
 template <int NX, int NU>
 __device__ void merit_block(const pdilqr_srbd_model& md, const float* x, const float* u,
                             const float* dx, const float* du, const float* xr, const float* ur,
@@ -385,7 +388,7 @@ __device__ void merit_block(const pdilqr_srbd_model& md, const float* x, const f
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int col = warp; col < 11; col += nw) {
         double aJ = 0.0, aT = 0.0, aD = 0.0;
-        float step = 0.f;
+        float step = 0.f, xmax = 0.f;
         const float a = col < 10 ? ldexpf(1.f, -col) : 0.f;
         for (int k = lane; k <= N; k += 32) {
             const bool term = k == N;
@@ -401,7 +404,10 @@ __device__ void merit_block(const pdilqr_srbd_model& md, const float* x, const f
             } else {
                 aJ += (double)srbd_stage_cost<NX>(md, xk, uk, ck, xrk, urk, term);
                 aD += (double)srbd_stage_dphi<NX>(md, xk, uk, dxk, duk, ck, xrk, urk, term);
-                for (int i = 0; i < NX; ++i) step = fmaxf(step, fabsf(dxk[i]));
+                for (int i = 0; i < NX; ++i) {
+                    step = fmaxf(step, fabsf(dxk[i]));
+                    xmax = fmaxf(xmax, fabsf(xk[i]));
+                }
                 if (!term)
                     for (int i = 0; i < NU; ++i) step = fmaxf(step, fabsf(duk[i]));
             }
@@ -420,6 +426,7 @@ __device__ void merit_block(const pdilqr_srbd_model& md, const float* x, const f
         aT = warp_sum(aT);
         aD = warp_sum(aD);
         step = warp_maxf(step);
+        xmax = warp_maxf(xmax);
         if (lane == 0) {
             if (col < 10) {
                 out[3 + col] = aJ;
@@ -429,6 +436,7 @@ __device__ void merit_block(const pdilqr_srbd_model& md, const float* x, const f
                 out[1] = aT;
                 out[2] = aD;
                 out[23] = (double)step;
+                out[25] = (double)xmax;
             }
         }
     }

@@ -53,6 +53,58 @@ class _KktOut(ctypes.Structure):
     _fields_ = [(k, _vp) for k in ("dx", "du", "dlam", "K", "k", "P", "p", "status", "resid")]
 
 
+class SrbdModel(ctypes.Structure):
+    _fields_ = [("nrob", ctypes.c_int32), ("w_form", ctypes.c_float),
+                ("d_form", ctypes.c_float * 48), ("mass", ctypes.c_float),
+                ("inertia", ctypes.c_float * 3), ("dt", ctypes.c_float),
+                ("gravity", ctypes.c_float), ("foot", ctypes.c_float * 12),
+                ("mu_fric", ctypes.c_float), ("bar_mu", ctypes.c_float),
+                ("bar_delta", ctypes.c_float), ("W", ctypes.c_float * 12),
+                ("Wu", ctypes.c_float * 12), ("WN", ctypes.c_float * 12)]
+
+
+class _Traj(ctypes.Structure):
+    _fields_ = [(k, _vp) for k in ("x", "u", "lam", "xref", "uref", "contact")]
+
+
+class _LQOut(ctypes.Structure):
+    _fields_ = [(k, _vp) for k in ("A", "B", "c", "Q", "R", "S", "q", "r")]
+
+
+class _SqpOpts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int32), ("tol_step", ctypes.c_float),
+                ("tol_theta", ctypes.c_float), ("c_armijo", ctypes.c_float),
+                ("theta_frac", ctypes.c_float), ("alpha_replay", _vp)]
+
+
+class _SqpInfo(ctypes.Structure):
+    _fields_ = [(k, _vp) for k in ("iters", "status", "alpha", "J", "theta")]
+
+
+def srbd_model(p: dict) -> SrbdModel:
+    """Pack a model-constant dict (see ``synth.srbd_params``) into the C struct."""
+    m = SrbdModel()
+    m.nrob = int(p.get("nrob", 1))
+    m.w_form = float(p.get("w_form", 0.0))
+    d = np.zeros(48, dtype=np.float64)
+    if "d_form" in p:
+        df = np.asarray(p["d_form"], dtype=np.float64).reshape(-1)
+        d[:df.size] = df
+    m.d_form[:] = d.tolist()
+    m.mass = p["mass"]
+    m.inertia[:] = [float(v) for v in p["inertia"]]
+    m.dt = p["dt"]
+    m.gravity = p["gravity"]
+    m.foot[:] = [float(v) for v in np.asarray(p["foot"]).reshape(12)]
+    m.mu_fric = p["mu_fric"]
+    m.bar_mu = p["bar_mu"]
+    m.bar_delta = p["bar_delta"]
+    m.W[:] = [float(v) for v in p["W"]]
+    m.Wu[:] = [float(v) for v in p["Wu"]]
+    m.WN[:] = [float(v) for v in p["WN"]]
+    return m
+
+
 _lib.pdilqr_status_string.restype = ctypes.c_char_p
 _lib.pdilqr_status_string.argtypes = [ctypes.c_int]
 _lib.pdilqr_plan_create.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Opts), ctypes.POINTER(_vp)]
@@ -62,6 +114,12 @@ _lib.pdilqr_plan_warps.restype = ctypes.c_int32
 for _f in ("pdilqr_kkt_scan_solve", "pdilqr_riccati_solve"):
     getattr(_lib, _f).argtypes = [_vp, ctypes.POINTER(_LQ), _vp, ctypes.POINTER(_KktOut), _vp]
 _lib.pdilqr_kkt_residual.argtypes = [_vp, ctypes.POINTER(_LQ), _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.pdilqr_linearize.argtypes = [_vp, ctypes.POINTER(SrbdModel), ctypes.POINTER(_Traj),
+                                  ctypes.POINTER(_LQOut), _vp]
+_lib.pdilqr_merit_eval.argtypes = [_vp, ctypes.POINTER(SrbdModel), ctypes.POINTER(_Traj),
+                                   _vp, _vp, _vp, _vp, _vp]
+_lib.pdilqr_solve.argtypes = [_vp, ctypes.POINTER(SrbdModel), ctypes.POINTER(_SqpOpts),
+                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_SqpInfo), _vp]
 
 
 def lib() -> ctypes.CDLL:
@@ -172,6 +230,61 @@ class Plan:
                                         _ptr(resid, torch.float64, "resid"), _stream(stream)),
                "pdilqr_kkt_residual")
         return resid
+
+
+    # ------------------------------------------------------- SRBD model
+    def _traj(self, traj: dict) -> _Traj:
+        return _Traj(_ptr(traj["x"], name="x"), _ptr(traj["u"], name="u"),
+                     _ptr(traj.get("lam"), name="lam"), _ptr(traj["xref"], name="xref"),
+                     _ptr(traj["uref"], name="uref"),
+                     _ptr(traj["contact"], torch.uint8, "contact"))
+
+    def linearize(self, model: SrbdModel, traj: dict, out: dict | None = None, stream=None) -> dict:
+        T, n, m = self.total, self.n, self.m
+        if out is None:
+            f = dict(device=traj["x"].device, dtype=torch.float32)
+            out = {"A": torch.empty(T, n, n, **f), "B": torch.empty(T, n, m, **f),
+                   "c": torch.empty(T, n, **f), "Q": torch.empty(T, n, n, **f),
+                   "R": torch.empty(T, m, m, **f), "S": torch.empty(T, m, n, **f),
+                   "q": torch.empty(T, n, **f), "r": torch.empty(T, m, **f)}
+        lo = _LQOut(*[_ptr(out.get(k), name=k) for k in ("A", "B", "c", "Q", "R", "S", "q", "r")])
+        _check(_lib.pdilqr_linearize(self._h, ctypes.byref(model), ctypes.byref(self._traj(traj)),
+                                     ctypes.byref(lo), _stream(stream)), "pdilqr_linearize")
+        return out
+
+    def merit_eval(self, model: SrbdModel, traj: dict, x0hat, dx, du, out=None, stream=None):
+        if out is None:
+            out = torch.zeros(self.count, 24, device=dx.device, dtype=torch.float64)
+        _check(_lib.pdilqr_merit_eval(self._h, ctypes.byref(model), ctypes.byref(self._traj(traj)),
+                                      _ptr(x0hat, name="x0hat"), _ptr(dx, name="dx"),
+                                      _ptr(du, name="du"), _ptr(out, torch.float64, "merit"),
+                                      _stream(stream)), "pdilqr_merit_eval")
+        return out
+
+    def solve(self, model: SrbdModel, x0hat, x, u, lam, xref, uref, contact, max_iters=10,
+              tol_step=0.0, tol_theta=0.0, c_armijo=1e-4, theta_frac=1e-2, alpha_replay=None,
+              info: dict | None = None, stream=None) -> dict:
+        """Run the fused SQP in place on (x, u, lam); returns the info tensors."""
+        dev = x.device
+        if info is None:
+            info = {"iters": torch.zeros(self.count, device=dev, dtype=torch.int32),
+                    "status": torch.full((self.count,), -1, device=dev, dtype=torch.int32),
+                    "alpha": torch.zeros(self.count, max_iters, device=dev, dtype=torch.float32),
+                    "J": torch.zeros(self.count, device=dev, dtype=torch.float64),
+                    "theta": torch.zeros(self.count, device=dev, dtype=torch.float64)}
+        o = _SqpOpts(int(max_iters), float(tol_step), float(tol_theta), float(c_armijo),
+                     float(theta_frac), _ptr(alpha_replay, name="alpha_replay"))
+        inf = _SqpInfo(_ptr(info["iters"], torch.int32, "iters"),
+                       _ptr(info["status"], torch.int32, "status"),
+                       _ptr(info.get("alpha"), name="alpha"),
+                       _ptr(info.get("J"), torch.float64, "J"),
+                       _ptr(info.get("theta"), torch.float64, "theta"))
+        _check(_lib.pdilqr_solve(self._h, ctypes.byref(model), ctypes.byref(o),
+                                 _ptr(x0hat, name="x0hat"), _ptr(x, name="x"), _ptr(u, name="u"),
+                                 _ptr(lam, name="lam"), _ptr(xref, name="xref"),
+                                 _ptr(uref, name="uref"), _ptr(contact, torch.uint8, "contact"),
+                                 ctypes.byref(inf), _stream(stream)), "pdilqr_solve")
+        return info
 
 
 def backward_error(resid: torch.Tensor) -> torch.Tensor:

@@ -1,0 +1,191 @@
+"""Parity of the SRBD linearisation, the line-search merit and the fused SQP
+with the FP64 oracle, through the C ABI.
+
+The oracle receives the same FP32-rounded inputs in FP64.  Tolerance: the
+target's 1e-4 relative error per block (normwise, infinity norm).  Full SQP
+runs are compared in replay mode (the GPU takes the oracle's step sizes) and
+free-running (the step sizes must agree and so must the iterates).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_07823_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+
+
+def r32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-30)
+
+
+def perturbed_batch(count, seed, Ns, nrob=1):
+    """SRBD problems with perturbed trajectories and costates (so every term of
+    the linearisation is exercised)."""
+    insts = []
+    g = np.random.default_rng(seed)
+    for i in range(count):
+        pr = synth.srbd_problem(Ns[i % len(Ns)], seed=seed + i, nrob=nrob)
+        pr["x"] = pr["x"] + g.normal(0, 0.05, pr["x"].shape)
+        pr["u"] = pr["u"] + g.normal(0, 4.0, pr["u"].shape)
+        pr["u"][-1] = 0.0
+        pr["lam"] = g.normal(0, 1.0, pr["lam"].shape)
+        insts.append(pr)
+    packed, Nv, off = synth.pack(insts, synth.SRBD_KEYS)
+    x0 = np.stack([p["x0hat"] for p in insts])
+    return insts, packed, Nv, off, x0
+
+
+def dev(packed):
+    out = {}
+    for k, v in packed.items():
+        if k == "contact":
+            out[k] = torch.tensor(np.asarray(v, dtype=np.uint8), device="cuda")
+        else:
+            out[k] = torch.tensor(np.asarray(v, dtype=np.float32), device="cuda")
+    return out
+
+
+@pytest.mark.parametrize("nrob", [1, 2])
+def test_linearize_parity(nrob):
+    from paper_2506_07823_b300 import pdilqr
+    n = 12 * nrob
+    insts, packed, Nv, off, x0 = perturbed_batch(3, 40 + nrob, [5, 9, 1], nrob)
+    prm = synth.srbd_params(nrob)
+    plan = pdilqr.Plan(n, n, Nv, off)
+    out = plan.linearize(pdilqr.srbd_model(prm), dev(packed))
+    torch.cuda.synchronize()
+    got = {k: v.double().cpu().numpy() for k, v in out.items()}
+    for i, pr in enumerate(insts):
+        N, o = int(Nv[i]), int(off[i])
+        ref = oracle.srbd_linearize(prm, r32(pr["x"]), r32(pr["u"]), r32(pr["lam"]),
+                                    r32(pr["xref"]), r32(pr["uref"]), pr["contact"])
+        sl = slice(o, o + N + 1)
+        for k in ("A", "B", "Q", "R", "q", "r"):
+            assert rel(got[k][sl], ref[k]) <= REL_TOL, (k, rel(got[k][sl], ref[k]))
+        # the defect is a difference of O(1) states: compare against their scale
+        assert np.abs(got["c"][sl] - ref["c"]).max() <= 1e-5 * max(1, np.abs(pr["x"]).max())
+        assert np.all(got["S"][sl] == 0)
+
+
+def test_merit_parity():
+    from paper_2506_07823_b300 import pdilqr
+    insts, packed, Nv, off, x0 = perturbed_batch(3, 7, [12, 30, 2])
+    prm = synth.srbd_params()
+    g = np.random.default_rng(1)
+    T = int(off[-1] + Nv[-1] + 1)
+    dx = (g.normal(0, 0.02, (T, 12))).astype(np.float32)
+    du = (g.normal(0, 2.0, (T, 12))).astype(np.float32)
+    for i, N in enumerate(Nv):
+        du[off[i] + N] = 0
+    d = dev(packed)
+    plan = pdilqr.Plan(12, 12, Nv, off)
+    mer = plan.merit_eval(pdilqr.srbd_model(prm), d, torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                          torch.tensor(dx, device="cuda"), torch.tensor(du, device="cuda"))
+    torch.cuda.synchronize()
+    mer = mer.cpu().numpy()
+    for i, pr in enumerate(insts):
+        N, o = int(Nv[i]), int(off[i])
+        sl = slice(o, o + N + 1)
+        x, u = r32(pr["x"]), r32(pr["u"])
+        args = (r32(pr["xref"]), r32(pr["uref"]), pr["contact"])
+        J0, th0 = oracle.srbd_merit(prm, r32(pr["x0hat"]), x, u, *args)
+        assert abs(mer[i, 0] - J0) <= 1e-5 * abs(J0)
+        assert abs(mer[i, 1] - th0) <= 1e-4 * th0 + 1e-5
+        # directional derivative by central differences of the oracle's cost
+        h = 1e-6
+        Jp, _ = oracle.srbd_merit(prm, r32(pr["x0hat"]), x + h * dx[sl], u + h * du[sl], *args)
+        Jm, _ = oracle.srbd_merit(prm, r32(pr["x0hat"]), x - h * dx[sl], u - h * du[sl], *args)
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(mer[i, 2] - fd) <= 1e-3 * max(1, abs(fd))
+        for t in range(10):
+            a = 2.0 ** -t
+            Ja, tha = oracle.srbd_merit(prm, r32(pr["x0hat"]), x + a * dx[sl].astype(np.float64),
+                                        u + a * du[sl].astype(np.float64), *args)
+            dJ = Ja - J0
+            assert abs(mer[i, 3 + t] - dJ) <= 1e-4 * abs(dJ) + 1e-6 * abs(J0), (t, mer[i, 3 + t], dJ)
+            assert abs(mer[i, 13 + t] - tha) <= 1e-4 * tha + 2e-5, (t, mer[i, 13 + t], tha)
+        assert mer[i, 23] == pytest.approx(max(np.abs(dx[sl]).max(), np.abs(du[o:o + N]).max()))
+
+
+def srbd_case(count, seed, Ns):
+    insts, packed, Nv, off, x0 = [], None, None, None, None
+    insts = [synth.srbd_problem(Ns[i % len(Ns)], seed=seed + i) for i in range(count)]
+    packed, Nv, off = synth.pack(insts, synth.SRBD_KEYS)
+    x0 = np.stack([p["x0hat"] for p in insts])
+    return insts, packed, Nv, off, x0
+
+
+def run_oracle(prm, pr, iters, alpha_replay=None):
+    return oracle.srbd_sqp(prm, r32(pr["x0hat"]), r32(pr["x"]), r32(pr["u"]), r32(pr["lam"]),
+                           r32(pr["xref"]), r32(pr["uref"]), pr["contact"], max_iters=iters,
+                           alpha_replay=alpha_replay)
+
+
+@pytest.mark.parametrize("warps", [4, 8, 16])
+@pytest.mark.parametrize("mode", ["replay", "free"])
+def test_sqp_parity(warps, mode):
+    from paper_2506_07823_b300 import pdilqr
+    iters = 10
+    insts, packed, Nv, off, x0 = srbd_case(4, 11, [25, 50, 75, 100])
+    prm = synth.srbd_params()
+    refs = [run_oracle(prm, pr, iters) for pr in insts]
+    d = dev(packed)
+    plan = pdilqr.Plan(12, 12, Nv, off, warps=warps)
+    replay = None
+    if mode == "replay":
+        replay = torch.tensor(np.stack([r[3]["alpha"] for r in refs]).astype(np.float32), device="cuda")
+    info = plan.solve(pdilqr.srbd_model(prm), torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                      d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                      max_iters=iters, alpha_replay=replay)
+    torch.cuda.synchronize()
+    st = info["status"].cpu().numpy()
+    assert np.all(st == 0), st
+    its = info["iters"].cpu().numpy()
+    if mode == "replay":
+        assert np.all(its == iters)
+    else:
+        # free-running, the FP32 iterate may stop early at its precision floor
+        assert np.all((its >= 6) & (its <= iters)), its
+    xs, us, ls = (d[k].double().cpu().numpy() for k in ("x", "u", "lam"))
+    al = info["alpha"].cpu().numpy()
+    for i, (xr, ur, lr, inf) in enumerate(refs):
+        N, o = int(Nv[i]), int(off[i])
+        sl = slice(o, o + N + 1)
+        if mode == "replay":
+            assert np.array_equal(al[i], inf["alpha"].astype(np.float32))
+        else:
+            # Step sizes must agree while the iterate's constraint violation is
+            # well above the FP32 storage floor of the states (~1e-6 summed
+            # over the horizon); below it the FP32 and FP64 filter tests may
+            # legitimately differ (the final iterate is still compared).
+            big = (inf["theta_it"] > 1e-4)[:its[i]]
+            assert np.array_equal(al[i][:its[i]][big], inf["alpha"][:its[i]][big].astype(np.float32)), (al[i], inf)
+        assert rel(xs[sl], xr) <= REL_TOL, rel(xs[sl], xr)
+        assert rel(us[o:o + N], ur[:N]) <= REL_TOL, rel(us[o:o + N], ur[:N])
+        assert rel(ls[sl], lr) <= REL_TOL, rel(ls[sl], lr)
+        J, th = info["J"][i].item(), info["theta"][i].item()
+        assert abs(J - inf["J"]) <= 1e-4 * abs(inf["J"])
+        assert th <= 1e-3
+
+
+def test_sqp_stops_on_tolerance():
+    from paper_2506_07823_b300 import pdilqr
+    insts, packed, Nv, off, x0 = srbd_case(2, 3, [30])
+    prm = synth.srbd_params()
+    d = dev(packed)
+    plan = pdilqr.Plan(12, 12, Nv, off)
+    info = plan.solve(pdilqr.srbd_model(prm), torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                      d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                      max_iters=30, tol_step=1e-2, tol_theta=1e-2)
+    torch.cuda.synchronize()
+    it = info["iters"].cpu().numpy()
+    assert np.all(it < 30) and np.all(it >= 2), it
+    assert np.all(info["status"].cpu().numpy() == 0)
