@@ -1,0 +1,518 @@
+#!/usr/bin/env python3
+"""Benchmark: batched primal-dual iLQR MPC solves on one B300 (and N GPUs).
+
+Workload (one step): 4096 single-rigid-body quadruped MPC problems with
+horizons drawn from {25, 50, 75, 100} (n = m = 12, dt = 0.02 s, trot
+contact schedule, friction-cone barrier), each solved by 10 SQP iterations
+of the fused kernel (linearisation + LQ KKT solve by the parallel scan +
+parallel line search + update) in one launch.  The metric counts KKT solves
+(one per SQP iteration per instance) per second.
+
+The JSON line also reports the single-instance latencies (one N = 50
+problem, CUDA-graph replays: the MPC tick of the paper), the comparators
+(sequential Riccati in the same fused kernel, and a plain sequential-Riccati
+KKT kernel launched once per instance), the roofline of the fused kernel,
+the end-to-end figure through the C ABI with host buffers, the FP64 oracle
+timed on the host cores, and the SM clocks seen during the timed region.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run (one rank per GPU); each rank
+solves its own batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2506_07823_b300 import synth  # noqa: E402  (no GPU code)
+
+METRIC = ("KKT solves/s and p99 solve latency at ≤1e-4 vs FP64 oracle, scan vs seq. "
+          "Riccati, 1×B300")
+UNIT = "KKT solves/s"
+COUNT = 4096
+HORIZONS = (25, 50, 75, 100)
+ITERS = 10
+SEED = 0
+WORKLOAD = "srbd_batched_mpc"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sqp_kernel_traffic.json")
+KERNEL_SOURCES = ["dev_linalg.cuh", "kkt_scan.cuh", "srbd.cuh", "sqp.cuh"]
+
+# FP32 FMA peak of a B300 from its unit counts: 148 SMs x 128 FP32 lanes x
+# 2 flop x 2.032 GHz (maximum SM clock).
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def flops_per_stage(n: int) -> float:
+    """Algorithmic flops of one LQ KKT solve per stage for n = m, the
+    work-efficient scan (combines in both sweeps, element build, policy,
+    trajectory): about 50 n^3."""
+    return 50.0 * n ** 3
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_07823_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------- CPU oracle
+def _oracle_worker(args):
+    import oracle  # test infrastructure: only the CPU-baseline leg runs it
+    prm, items = args
+    its = 0
+    for pr in items:
+        _, _, _, info = oracle.srbd_sqp(prm, pr["x0hat"], pr["x"], pr["u"], pr["lam"],
+                                        pr["xref"], pr["uref"], pr["contact"], max_iters=ITERS)
+        its += info["iters"]
+    return its
+
+
+def oracle_pool(cores: int):
+    return mp.get_context("spawn").Pool(cores)
+
+
+def oracle_run(pool, cores: int, insts: list) -> tuple[int, float]:
+    """Solve ``insts`` with the FP64 oracle on ``cores`` processes; returns
+    (KKT solves, wall seconds)."""
+    prm = synth.srbd_params()
+    chunks = [insts[i::cores] for i in range(cores)]
+    t0 = time.perf_counter()
+    its = sum(pool.map(_oracle_worker, [(prm, c) for c in chunks if c]))
+    return its, time.perf_counter() - t0
+
+
+def host_cores() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except Exception:
+        return max(1, os.cpu_count() or 1)
+
+
+def sample_size(cores: int) -> int:
+    # about 10-30 s of oracle work (roughly 1.2k KKT solves/s per core)
+    return int(min(COUNT, max(64, cores * 300)))
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock samples (every 200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def build_device_batch(torch, insts, packed, Nv, off, x0, dev):
+    t = {}
+    for k in ("x", "u", "lam", "xref", "uref"):
+        t[k] = torch.tensor(np.asarray(packed[k], dtype=np.float32), device=dev)
+    t["contact"] = torch.tensor(np.asarray(packed["contact"], dtype=np.uint8), device=dev)
+    t["x0hat"] = torch.tensor(np.asarray(x0, dtype=np.float32), device=dev)
+    return t
+
+
+def event_times(torch, fn, reps, stream, before=None):
+    """Per-call device times (ms) with CUDA events on ``stream``."""
+    out = []
+    for _ in range(reps):
+        if before:
+            before()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def pct(v, q):
+    return float(np.percentile(np.asarray(v), q))
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2506_07823_b300 import pdilqr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # CPU baseline pool: spawned before the first GPU kernel
+    cores = host_cores()
+    pool = oracle_pool(cores) if (rank == 0 and not args.no_cpu) else None
+
+    insts, packed, Nv, off, x0 = synth.srbd_batch(args.count, seed=SEED + rank * args.count,
+                                                  Ns_choices=HORIZONS)
+    total_stages = int(Nv.sum() + len(Nv))
+    prm = synth.srbd_params()
+    md = pdilqr.srbd_model(prm)
+    base = build_device_batch(torch, insts, packed, Nv, off, x0, dev)
+    work = {k: v.clone() for k, v in base.items()}
+
+    def reset():
+        for k in ("x", "u", "lam"):
+            work[k].copy_(base[k], non_blocking=True)
+
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.zero_()
+
+    # --- autotune the warps per instance on this batch (one solve each)
+    plans = {}
+    tune = {}
+    for w in (4, 8, 16):
+        try:
+            plans[w] = pdilqr.Plan(12, 12, Nv, off, warps=w)
+        except pdilqr.PdilqrError:
+            continue
+        def solve_w(p=plans[w]):
+            return p.solve(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"],
+                           work["uref"], work["contact"], max_iters=ITERS)
+        reset()
+        solve_w()
+        torch.cuda.synchronize()
+        tune[w] = min(event_times(torch, solve_w, 2, stream, before=lambda: (reset(), flush())))
+    W = min(tune, key=tune.get)
+    plan = plans[W]
+    info = {"iters": torch.zeros(plan.count, device=dev, dtype=torch.int32),
+            "status": torch.zeros(plan.count, device=dev, dtype=torch.int32),
+            "alpha": None, "J": None, "theta": None}
+
+    def solve():
+        plan.solve(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"],
+                   work["uref"], work["contact"], max_iters=ITERS, info=info)
+
+    for _ in range(args.warmup):
+        reset()
+        solve()
+    torch.cuda.synchronize()
+
+    # --- timed region: K solves; reset and L2 flush between them, outside the events
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    times = event_times(torch, solve, args.steps, stream, before=lambda: (reset(), flush()))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    kkt_per_step = int(info["iters"].sum().item())
+    st = info["status"].cpu().numpy()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        k = torch.tensor([kkt_per_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(k)
+        kkt_all = float(k.item())
+    else:
+        kkt_all = float(kkt_per_step)
+    value = kkt_all / (ms / 1e3)
+
+    result = None
+    if rank == 0:
+        n = 12
+        achieved = flops_per_stage(n) * total_stages * (kkt_per_step / plan.count) / (ms / 1e3) / 1e12
+        traffic = None
+        try:
+            tr = json.load(open(TRAFFIC_FILE))
+            if tr.get("source_hash") == kernel_source_hash():
+                traffic = tr["bytes_per_launch_full"]
+        except Exception:
+            traffic = None
+        extras = measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args)
+        e2e = measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args)
+        cpu = None
+        if pool is not None:
+            sample = insts[:sample_size(cores)]
+            its, secs = oracle_run(pool, cores, sample)
+            cpu = {"value": its / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{len(sample)} of the {args.count} instances, one 10-iteration "
+                             f"SQP solve each, FP64 C oracle, {cores} processes, {secs:.1f} s"}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (FP64 line-search sums)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances_per_gpu": args.count,
+                       "horizons": list(HORIZONS), "n": 12, "m": 12, "sqp_iters": ITERS,
+                       "stages_per_gpu": total_stages, "warps_per_instance": W,
+                       "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()},
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas{world}"},
+            "latency_ms": {"batch_p50": pct(times, 50), "batch_p99": pct(times, 99),
+                           **extras["latency"]},
+            "comparators": extras["comparators"],
+            "status_counts": {str(int(s)): int((st == s).sum()) for s in np.unique(st)},
+            "kkt_solves_per_step": kkt_all,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": traffic,
+                         "kernel": f"sqp_kernel<12,12,{W}>",
+                         "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 x 2.032 GHz"},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": args.steps,
+            "wall_s_timed_region": wall,
+        }
+    if pool is not None:
+        pool.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args):
+    """Single-instance latencies (MPC tick) and the comparators."""
+    lat, comp = {}, {}
+    # one N = 50 problem, the paper's SRBD MPC tick
+    pr = synth.srbd_problem(50, seed=SEED)
+    pk, Nv1, off1 = synth.pack([pr], synth.SRBD_KEYS)
+    one = build_device_batch(torch, [pr], pk, Nv1, off1, pr["x0hat"][None], dev)
+    w1 = {k: v.clone() for k, v in one.items()}
+    reps = args.latency_reps
+    for name, warps in (("scan_sqp_single", 16), ("riccati_sqp_single", 1)):
+        p1 = pdilqr.Plan(12, 12, Nv1, off1, warps=warps)
+        inf1 = {"iters": torch.zeros(1, device=dev, dtype=torch.int32),
+                "status": torch.zeros(1, device=dev, dtype=torch.int32),
+                "alpha": None, "J": None, "theta": None}
+
+        def step(p1=p1, inf1=inf1):
+            for k in ("x", "u", "lam"):
+                w1[k].copy_(one[k], non_blocking=True)
+            p1.solve(md, w1["x0hat"], w1["x"], w1["u"], w1["lam"], w1["xref"], w1["uref"],
+                     w1["contact"], max_iters=ITERS, info=inf1)
+        step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(10):
+            g.replay()
+        t = event_times(torch, g.replay, reps, stream)
+        lat[name + "_p50"] = pct(t, 50)
+        lat[name + "_p99"] = pct(t, 99)
+    # LQ KKT solves alone on the linearisation of the 4096-instance batch
+    lq = plan.linearize(md, base)
+    lq["S"] = None
+    s = (base["x0hat"] - base["x"][torch.tensor(plan.stage_off, device=dev)]).contiguous()
+    out = plan.alloc_out(device=dev)
+    for name, fn in (("scan_kkt_batched", plan.kkt_scan_solve),
+                     ("riccati_kkt_batched", plan.riccati_solve)):
+        fn(lq, s, out=out)
+        torch.cuda.synchronize()
+        t = event_times(torch, lambda fn=fn: fn(lq, s, out=out), 5, stream)
+        comp[name] = {"kkt_solves_per_s": plan.count / (np.mean(t) / 1e3), "ms": float(np.mean(t))}
+    # the plain comparator: one sequential-Riccati KKT solve per launch
+    sample = min(args.count, args.comparator_sample)
+    plans1, lqs, ss, outs = [], [], [], []
+    for i in range(sample):
+        N, o = int(plan.N[i]), int(plan.stage_off[i])
+        p1 = pdilqr.Plan(12, 12, [N], [0])
+        plans1.append(p1)
+        lqs.append({k: (v[o:o + N + 1].contiguous() if v is not None else None) for k, v in lq.items()})
+        ss.append(s[i:i + 1].contiguous())
+        outs.append(p1.alloc_out(device=dev))
+    for i in range(sample):
+        plans1[i].riccati_solve(lqs[i], ss[i], out=outs[i])
+    torch.cuda.synchronize()
+
+    def one_per_launch():
+        for i in range(sample):
+            plans1[i].riccati_solve(lqs[i], ss[i], out=outs[i])
+    t = event_times(torch, one_per_launch, 3, stream)
+    per = np.mean(t) / sample
+    comp["riccati_kkt_one_instance_per_launch"] = {
+        "kkt_solves_per_s": 1e3 / per, "ms_per_solve": per,
+        "sample": f"{sample} instances of the batch, one launch each, back to back"}
+    # single-instance KKT latency, scan (16 warps) vs sequential Riccati kernel
+    i0 = 0
+    N0 = int(plan.N[i0])
+    o0 = int(plan.stage_off[i0])
+    p16 = pdilqr.Plan(12, 12, [N0], [0], warps=16)
+    lq0 = {k: (v[o0:o0 + N0 + 1].contiguous() if v is not None else None) for k, v in lq.items()}
+    o16 = p16.alloc_out(device=dev)
+    for name, fn in (("scan_kkt_single", p16.kkt_scan_solve), ("riccati_kkt_single", p16.riccati_solve)):
+        fn(lq0, ss[0], out=o16)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn(lq0, ss[0], out=o16)
+        for _ in range(10):
+            g.replay()
+        t = event_times(torch, g.replay, reps, stream)
+        lat[name + "_p50"] = pct(t, 50)
+        lat[name + "_p99"] = pct(t, 99)
+    lat["single_horizon"] = {"sqp": 50, "kkt": N0}
+    return {"latency": lat, "comparators": comp}
+
+
+def measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args):
+    """The same metric through the C ABI with host buffers: every step copies
+    the problem (x0hat, warm start x, u, lam, references, contact) from pinned
+    host memory, solves, and reads the solution (x, u) and status back."""
+    host = {k: v.cpu().pin_memory() for k, v in base.items()}
+    devb = {k: torch.empty_like(v) for k, v in base.items()}
+    out_x = torch.empty_like(host["x"]).pin_memory()
+    out_u = torch.empty_like(host["u"]).pin_memory()
+    info = {"iters": torch.zeros(plan.count, device=dev, dtype=torch.int32),
+            "status": torch.zeros(plan.count, device=dev, dtype=torch.int32),
+            "alpha": None, "J": None, "theta": None}
+    out_st = torch.empty(plan.count, dtype=torch.int32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = out_x.numel() * 4 + out_u.numel() * 4 + out_st.numel() * 4
+
+    def step():
+        for k in host:
+            devb[k].copy_(host[k], non_blocking=True)
+        plan.solve(md, devb["x0hat"], devb["x"], devb["u"], devb["lam"], devb["xref"],
+                   devb["uref"], devb["contact"], max_iters=ITERS, info=info)
+        out_x.copy_(devb["x"], non_blocking=True)
+        out_u.copy_(devb["u"], non_blocking=True)
+        out_st.copy_(info["status"], non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t = event_times(torch, step, max(3, args.steps // 2), stream)
+    kkt = int(info["iters"].sum().item())
+    return {"value": kkt / (np.mean(t) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.mean(t))}
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    cores = host_cores()
+    pool = oracle_pool(cores)
+    insts, packed, Nv, off, x0 = synth.srbd_batch(args.count, seed=SEED, Ns_choices=HORIZONS)
+    sample = insts[:sample_size(cores)]
+    for _ in range(args.warmup):
+        oracle_run(pool, cores, sample[:cores])
+    tot_its, tot_s, per = 0, 0.0, []
+    for _ in range(args.steps):
+        its, secs = oracle_run(pool, cores, sample)
+        tot_its += its
+        tot_s += secs
+        per.append(secs)
+    pool.close()
+    value = tot_its / tot_s
+    desc = (f"{len(sample)} of the {args.count} instances per step, one 10-iteration SQP "
+            f"solve each, FP64 C oracle on {cores} host processes")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances_per_gpu": args.count,
+                       "horizons": list(HORIZONS), "n": 12, "m": 12, "sqp_iters": ITERS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--count", type=int, default=COUNT)
+    ap.add_argument("--latency-reps", type=int, default=200)
+    ap.add_argument("--comparator-sample", type=int, default=512)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

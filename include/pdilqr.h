@@ -76,7 +76,10 @@ typedef struct {
 
 typedef struct {
     int32_t warps;      /* warps per instance for the scan: 4, 8 or 16;      */
-                        /* 0 picks by the longest horizon of the batch      */
+                        /* 0 picks by the longest horizon of the batch;     */
+                        /* 1 runs the whole horizon in one chunk, i.e. the  */
+                        /* sequential Riccati recursion inside the same     */
+                        /* kernels (the comparator of the fused solver)     */
     int32_t refine;     /* 0: plain FP32 solve; 1: one refinement step      */
                         /* against the FP64-evaluated KKT residual          */
 } pdilqr_opts;

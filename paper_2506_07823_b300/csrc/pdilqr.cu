@@ -79,6 +79,7 @@ template <int NX, int NU>
 static size_t scan_smem(int warps)
 {
     switch (warps) {
+        case 1: return ScanSmem<NX, NU, 1>::BYTES;
         case 4: return ScanSmem<NX, NU, 4>::BYTES;
         case 8: return ScanSmem<NX, NU, 8>::BYTES;
         case 16: return ScanSmem<NX, NU, 16>::BYTES;
@@ -90,6 +91,7 @@ template <int NX, int NU>
 static cudaError_t launch_scan(const KktArgs& a, int warps, cudaStream_t st)
 {
     switch (warps) {
+        case 1: return launch_scan_w<NX, NU, 1>(a, st);
         case 4: return launch_scan_w<NX, NU, 4>(a, st);
         case 8: return launch_scan_w<NX, NU, 8>(a, st);
         case 16: return launch_scan_w<NX, NU, 16>(a, st);
@@ -171,6 +173,7 @@ template <int NX, int NU>
 static cudaError_t launch_sqp(const SqpArgs& a, int warps, cudaStream_t st)
 {
     switch (warps) {
+        case 1: return launch_sqp_w<NX, NU, 1>(a, st);
         case 4: return launch_sqp_w<NX, NU, 4>(a, st);
         case 8: return launch_sqp_w<NX, NU, 8>(a, st);
         case 16: return launch_sqp_w<NX, NU, 16>(a, st);
@@ -182,6 +185,7 @@ template <int NX, int NU>
 static size_t sqp_smem(int warps)
 {
     switch (warps) {
+        case 1: return SqpSmem<NX, NU, 1>::BYTES;
         case 4: return SqpSmem<NX, NU, 4>::BYTES;
         case 8: return SqpSmem<NX, NU, 8>::BYTES;
         case 16: return SqpSmem<NX, NU, 16>::BYTES;
@@ -284,7 +288,8 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
         if (hoff[pa] + hN[pa] + 1 > hoff[pb]) return PDILQR_E_INVALID_ARG;
     }
     pl->warps = (o && o->warps) ? o->warps : pick_warps(pl->ops, pl->maxN);
-    if (pl->warps != 4 && pl->warps != 8 && pl->warps != 16) return PDILQR_E_INVALID_ARG;
+    if (pl->warps != 1 && pl->warps != 4 && pl->warps != 8 && pl->warps != 16)
+        return PDILQR_E_INVALID_ARG;
     pl->refine = (o && o->refine) ? 1 : 0;
     // longest horizons first: the tail of the grid holds the short instances
     std::vector<int32_t> order(b->count);

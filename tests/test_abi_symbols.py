@@ -51,3 +51,5 @@ def test_plan_rejects_bad_batches_without_gpu_work():
         pdilqr.Plan(4, 2, [0], [0])              # empty horizon
     with pytest.raises(pdilqr.PdilqrError):
         pdilqr.Plan(4, 2, [4], [0], warps=5)     # unsupported warp count
+    with pytest.raises(pdilqr.PdilqrError):
+        pdilqr.Plan(4, 2, [4], [0], warps=2)
