@@ -17,6 +17,39 @@ namespace pdl {
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int round4(int a) { return (a + 3) & ~3; }
 
+// ------------------------------------------------ asynchronous copies
+// Global -> shared copies that bypass registers (cp.async): a group issues
+// every copy of a tile, then waits once, so all loads of the tile are in
+// flight together.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory"); }
+
+// Copy COUNT floats of one stage (global offset base + gs * COUNT) into shared
+// memory with the group's threads.  16-byte copies when every address of the
+// tile is 16-byte aligned by construction (COUNT a multiple of 4 and a 16-byte
+// aligned shared destination and global base), 4-byte copies otherwise.
+template <int COUNT, int NT, bool VEC>
+__device__ __forceinline__ void stage_copy(int t, float* dst, const float* src)
+{
+    if constexpr (VEC && COUNT % 4 == 0) {
+        for (int e = t; e < COUNT / 4; e += NT) cp_async16(dst + 4 * e, src + 4 * e);
+    } else {
+        for (int e = t; e < COUNT; e += NT) cp_async4(dst + e, src + e);
+    }
+}
+
 template <int NT>
 struct Grp {
     int t;    // rank inside the group
@@ -153,7 +186,7 @@ __device__ __forceinline__ void symmetrize(const Grp<NT>& g, float* M, int ld)
 // dinv[j] receives 1 / L[j][j].  Returns false (uniformly over the group) if
 // a pivot is not positive and finite; the factor is then meaningless.
 template <int M, int NT>
-__device__ bool chol(const Grp<NT>& g, float* L, int ld, float* dinv)
+__device__ bool chol_generic(const Grp<NT>& g, float* L, int ld, float* dinv)
 {
     bool ok = true;
     for (int j = 0; j < M; ++j) {
@@ -180,8 +213,8 @@ __device__ bool chol(const Grp<NT>& g, float* L, int ld, float* dinv)
 
 // Solve L Y = X in place (X is M x NC); L lower triangular, dinv = 1/diag.
 template <int M, int NC, int NT>
-__device__ void trsm_lower(const Grp<NT>& g, const float* L, int ld, const float* dinv,
-                           float* X, int ldx)
+__device__ void trsm_lower_generic(const Grp<NT>& g, const float* L, int ld, const float* dinv,
+                                   float* X, int ldx)
 {
     for (int i = 0; i < M; ++i) {
         for (int c = g.t; c < NC; c += NT) X[i * ldx + c] *= dinv[i];
@@ -197,8 +230,8 @@ __device__ void trsm_lower(const Grp<NT>& g, const float* L, int ld, const float
 
 // Solve L^T Y = X in place (X is M x NC).
 template <int M, int NC, int NT>
-__device__ void trsm_lower_t(const Grp<NT>& g, const float* L, int ld, const float* dinv,
-                             float* X, int ldx)
+__device__ void trsm_lower_t_generic(const Grp<NT>& g, const float* L, int ld, const float* dinv,
+                                     float* X, int ldx)
 {
     for (int i = M - 1; i >= 0; --i) {
         for (int c = g.t; c < NC; c += NT) X[i * ldx + c] *= dinv[i];
@@ -216,7 +249,7 @@ __device__ void trsm_lower_t(const Grp<NT>& g, const float* L, int ld, const flo
 // On exit columns N..N+NR-1 hold Mx^{-1} RHS.  Returns false (uniformly) if
 // a pivot is zero or not finite.
 template <int N, int NR, int NT>
-__device__ bool gj_solve(const Grp<NT>& g, float* G, int ld)
+__device__ bool gj_solve_generic(const Grp<NT>& g, float* G, int ld)
 {
     constexpr int W = N + NR;
     bool ok = true;
@@ -250,6 +283,207 @@ __device__ bool gj_solve(const Grp<NT>& g, float* G, int ld)
         g.sync();
     }
     return ok;
+}
+
+// ---------------------------------------------------------------------------
+// One-warp versions: operands live in registers, one row or one column per
+// lane, so the sequential steps need no index arithmetic and few barriers.
+
+// Right-looking Cholesky, lane i holds row i (M <= 32).  Per column j: lane j
+// takes the square root of its pivot, lanes below scale their entry and
+// publish it, then every lane applies the rank-one update to its own row.
+template <int M>
+__device__ bool chol_warp(int lane, float* L, int ld, float* dinv, float* colbuf)
+{
+    static_assert(M <= 32, "one row per lane");
+    float row[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) row[k] = (lane < M) ? L[lane * ld + k] : 0.f;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        if (lane == j) {
+            const float d = row[j];
+            const float s = sqrtf(fmaxf(d, 1e-30f));
+            colbuf[M] = (d > 0.f && isfinite(d)) ? 1.f : 0.f;
+            colbuf[M + 1] = s;
+            colbuf[M + 2] = 1.f / s;
+        }
+        __syncwarp();
+        ok = ok && (colbuf[M] != 0.f);
+        const float inv = colbuf[M + 2];
+        if (lane == j) row[j] = colbuf[M + 1];
+        if (lane > j && lane < M) {
+            row[j] *= inv;
+            colbuf[lane] = row[j];
+        }
+        __syncwarp();
+        if (lane > j && lane < M) {
+            const float lij = row[j];
+#pragma unroll
+            for (int k = j + 1; k < M; ++k) row[k] -= lij * colbuf[k];
+        }
+        if (lane == j) dinv[j] = inv;
+        __syncwarp();
+    }
+    if (lane < M) {
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (k <= lane) L[lane * ld + k] = row[k];
+    }
+    __syncwarp();
+    return ok;
+}
+
+// L Y = X with one right-hand side per lane (forward substitution in
+// registers); L is read by broadcast.  NC right-hand sides, any count.
+template <int M, int NC>
+__device__ void trsm_lower_warp(int lane, const float* L, int ld, const float* dinv, float* X, int ldx)
+{
+    for (int c = lane; c < NC; c += 32) {
+        float y[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) y[i] = X[i * ldx + c];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            float v = y[i];
+#pragma unroll
+            for (int l = 0; l < i; ++l) v -= L[i * ld + l] * y[l];
+            y[i] = v * dinv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) X[i * ldx + c] = y[i];
+    }
+    __syncwarp();
+}
+
+// L^T Y = X, backward substitution per lane.
+template <int M, int NC>
+__device__ void trsm_lower_t_warp(int lane, const float* L, int ld, const float* dinv, float* X, int ldx)
+{
+    for (int c = lane; c < NC; c += 32) {
+        float y[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) y[i] = X[i * ldx + c];
+#pragma unroll
+        for (int i = M - 1; i >= 0; --i) {
+            float v = y[i];
+#pragma unroll
+            for (int l = i + 1; l < M; ++l) v -= L[l * ld + i] * y[l];
+            y[i] = v * dinv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) X[i * ldx + c] = y[i];
+    }
+    __syncwarp();
+}
+
+// Gauss-Jordan with partial pivoting, one column of [Mx | RHS] per lane
+// (two for lanes below W - 32).  Step k: lane k picks the pivot in its column,
+// swaps, and publishes the column (double-buffered shared slot); every lane
+// swaps the same rows of its columns, normalises the pivot row entry and
+// eliminates.  Only columns right of the pivot are updated.  On exit the RHS
+// columns hold Mx^{-1} RHS.  colbuf: 2 * (N + 1) floats.
+template <int N, int NR>
+__device__ bool gj_warp(int lane, float* G, int ld, float* colbuf)
+{
+    constexpr int W = N + NR;
+    constexpr int NQ = (W + 31) / 32;
+    static_assert(N <= 32 && NQ <= 2, "pivot columns owned by single lanes");
+    float c[NQ][N];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int j = lane + 32 * q;
+#pragma unroll
+        for (int i = 0; i < N; ++i) c[q][i] = (j < W) ? G[i * ld + j] : 0.f;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        float* cb = colbuf + (k & 1) * (N + 1);
+        if (lane == k) {
+            int piv = k;
+            float best = fabsf(c[0][k]);
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) {
+                const float v = fabsf(c[0][i]);
+                if (v > best) { best = v; piv = i; }
+            }
+            float vp = c[0][k];
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) vp = (piv == i) ? c[0][i] : vp;
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) c[0][i] = (piv == i) ? c[0][k] : c[0][i];
+            c[0][k] = vp;
+#pragma unroll
+            for (int i = 0; i < N; ++i) cb[i] = c[0][i];
+            cb[N] = __int_as_float(piv);
+        }
+        __syncwarp();
+        const int piv = __float_as_int(cb[N]);
+        const float pk = cb[k];
+        ok = ok && (fabsf(pk) > 1e-30f) && isfinite(pk);
+        const float inv = 1.f / pk;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = lane + 32 * q;
+            if (j <= k || j >= W) continue;
+            float vp = c[q][k];
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) vp = (piv == i) ? c[q][i] : vp;
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) c[q][i] = (piv == i) ? c[q][k] : c[q][i];
+            const float r = vp * inv;
+            c[q][k] = r;
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+                if (i != k) c[q][i] -= cb[i] * r;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int j = lane + 32 * q;
+        if (j >= N && j < W) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) G[i * ld + j] = c[q][i];
+        }
+    }
+    __syncwarp();
+    return ok;
+}
+
+// ---------------------------------------------------------------- dispatch
+// One-warp groups use the register versions (they need a small shared
+// scratch: `wsc`, at least 2 * (max(M, N) + 3) floats); wider groups use the
+// step-synchronous versions.
+template <int M, int NT>
+__device__ __forceinline__ bool chol(const Grp<NT>& g, float* L, int ld, float* dinv, float* wsc)
+{
+    if constexpr (NT == 32 && M <= 32) return chol_warp<M>(g.t, L, ld, dinv, wsc);
+    else return chol_generic<M, NT>(g, L, ld, dinv);
+}
+
+template <int M, int NC, int NT>
+__device__ __forceinline__ void trsm_lower(const Grp<NT>& g, const float* L, int ld,
+                                           const float* dinv, float* X, int ldx)
+{
+    if constexpr (NT == 32 && M <= 32) trsm_lower_warp<M, NC>(g.t, L, ld, dinv, X, ldx);
+    else trsm_lower_generic<M, NC, NT>(g, L, ld, dinv, X, ldx);
+}
+
+template <int M, int NC, int NT>
+__device__ __forceinline__ void trsm_lower_t(const Grp<NT>& g, const float* L, int ld,
+                                             const float* dinv, float* X, int ldx)
+{
+    if constexpr (NT == 32 && M <= 32) trsm_lower_t_warp<M, NC>(g.t, L, ld, dinv, X, ldx);
+    else trsm_lower_t_generic<M, NC, NT>(g, L, ld, dinv, X, ldx);
+}
+
+template <int N, int NR, int NT>
+__device__ __forceinline__ bool gj_solve(const Grp<NT>& g, float* G, int ld, float* wsc)
+{
+    if constexpr (NT == 32 && N <= 32 && (N + NR + 31) / 32 <= 2) return gj_warp<N, NR>(g.t, G, ld, wsc);
+    else return gj_solve_generic<N, NR, NT>(g, G, ld);
 }
 
 }  // namespace pdl

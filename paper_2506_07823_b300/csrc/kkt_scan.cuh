@@ -51,10 +51,14 @@ struct KktArgs {
 
 // ------------------------------------------------------------------ layouts
 template <int NX, int NU>
-struct StageL {  // one stage of LQ data staged in shared memory
-    static constexpr int A = 0, B = A + NX * NX, Q = B + NX * NU, R = Q + NX * NX,
-                         S = R + NU * NU, c = S + NU * NX, q = c + NX, r = q + NX,
-                         SIZE = round4(r + NU);
+struct StageL {  // one stage of LQ data staged in shared memory (every block
+                 // starts on a 16-byte boundary); IN is the model-input area
+                 // of sources that linearise on the fly
+    static constexpr int A = 0, B = round4(A + NX * NX), Q = round4(B + NX * NU),
+                         R = round4(Q + NX * NX), S = round4(R + NU * NU),
+                         c = round4(S + NU * NX), q = round4(c + NX), r = round4(q + NX),
+                         IN = round4(r + NU),
+                         SIZE = round4(IN + 5 * round4(NX) + 2 * round4(NU) + round4(NX / 12 + 1));
 };
 
 template <int NX>
@@ -64,49 +68,47 @@ struct ElemL {  // CVF element (A, C, b, P, p); a value function uses P, p only,
                          p = 3 * NX * NX + NX, SIZE = round4(3 * NX * NX + 2 * NX);
 };
 
+// (Wk: small scratch of the one-warp factorisations, 2 (dim + 3) floats)
 template <int NX, int NU>
 struct BuildL {  // scratch of the element build
     static constexpr int Lr = 0, dinv = Lr + NU * NU, Z = round4(dinv + NU),
-                         Y = Z + NU * NX, SIZE = round4(Y + NU * (NX + 1));
+                         Y = Z + NU * NX, Wk = round4(Y + NU * (NX + 1)),
+                         SIZE = round4(Wk + 2 * (NU + 3));
 };
 
 template <int NX>
 struct CombL {  // scratch of a combine
     static constexpr int LDG = 3 * NX + 1;
     static constexpr int G = 0, T = round4(NX * LDG), U = T + NX * NX, w = U + NX * NX,
-                         SIZE = round4(w + NX);
+                         Wk = round4(w + NX), SIZE = round4(Wk + 2 * (NX + 3));
 };
 
 template <int NX, int NU>
 struct RicL {  // scratch of one Riccati step
     static constexpr int PB = 0, PA = PB + NX * NU, w = PA + NX * NX, G = round4(w + NX),
                          dinv = G + NU * NU, Y = round4(dinv + NU), Y2 = Y + NU * (NX + 1),
-                         SIZE = round4(Y2 + NU * (NX + 1));
+                         Wk = round4(Y2 + NU * (NX + 1)), SIZE = round4(Wk + 2 * (NU + 3));
 };
 
 // ------------------------------------------------------------ stage loading
+// All blocks of one stage are copied asynchronously and waited for once.
 template <int NX, int NU, int NT>
 __device__ __forceinline__ void load_stage(const Grp<NT>& g, float* st, const KktArgs& a,
                                            int64_t gs, bool terminal)
 {
     using L = StageL<NX, NU>;
-    const float* srcQ = a.Q + gs * NX * NX;
-    for (int e = g.t; e < NX * NX; e += NT) st[L::Q + e] = srcQ[e];
-    for (int e = g.t; e < NX; e += NT) st[L::q + e] = a.q[gs * NX + e];
+    stage_copy<NX * NX, NT, true>(g.t, st + L::Q, a.Q + gs * NX * NX);
+    stage_copy<NX, NT, true>(g.t, st + L::q, a.q + gs * NX);
     if (!terminal) {
-        const float* srcA = a.A + gs * NX * NX;
-        const float* srcB = a.B + gs * NX * NU;
-        const float* srcR = a.R + gs * NU * NU;
-        for (int e = g.t; e < NX * NX; e += NT) st[L::A + e] = srcA[e];
-        for (int e = g.t; e < NX * NU; e += NT) st[L::B + e] = srcB[e];
-        for (int e = g.t; e < NU * NU; e += NT) st[L::R + e] = srcR[e];
-        for (int e = g.t; e < NX; e += NT) st[L::c + e] = a.c[gs * NX + e];
-        for (int e = g.t; e < NU; e += NT) st[L::r + e] = a.r[gs * NU + e];
-        if (a.S) {
-            const float* srcS = a.S + gs * NU * NX;
-            for (int e = g.t; e < NU * NX; e += NT) st[L::S + e] = srcS[e];
-        }
+        stage_copy<NX * NX, NT, true>(g.t, st + L::A, a.A + gs * NX * NX);
+        stage_copy<NX * NU, NT, true>(g.t, st + L::B, a.B + gs * NX * NU);
+        stage_copy<NU * NU, NT, true>(g.t, st + L::R, a.R + gs * NU * NU);
+        stage_copy<NX, NT, true>(g.t, st + L::c, a.c + gs * NX);
+        stage_copy<NU, NT, true>(g.t, st + L::r, a.r + gs * NU);
+        if (a.S) stage_copy<NU * NX, NT, true>(g.t, st + L::S, a.S + gs * NU * NX);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     g.sync();
 }
 
@@ -152,7 +154,7 @@ __device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float
     if (has_S) copy<NU, NX, false, NT, false>(g, Y, LDY, st + L::S, NX);
     for (int i = g.t; i < NU; i += NT) Y[i * LDY + NX] = st[L::r + i];
     g.sync();
-    const bool ok = chol<NU, NT>(g, Lr, NU, dinv);
+    const bool ok = chol<NU, NT>(g, Lr, NU, dinv, scr + S::Wk);
     trsm_lower<NU, NX, NT>(g, Lr, NU, dinv, Z, NX);             // Z = L^-1 B^T
     if (has_S) {
         trsm_lower<NU, NX + 1, NT>(g, Lr, NU, dinv, Y, LDY);
@@ -205,7 +207,7 @@ __device__ bool combine_full(const Grp<NT>& g, const float* e1, const float* e2,
     g.sync();
     for (int i = g.t; i < NX; i += NT) G[i * LDG + i] += 1.f;   // M = I + C1 P2
     g.sync();
-    const bool ok = gj_solve<NX, 2 * NX + 1, NT>(g, G, LDG);
+    const bool ok = gj_solve<NX, 2 * NX + 1, NT>(g, G, LDG, scr + S::Wk);
     const float* XA = G + NX;       // M^-1 A1
     const float* XC = G + 2 * NX;   // M^-1 C1
     const float* xb = G + 3 * NX;   // M^-1 (b1 - C1 p2)
@@ -241,7 +243,7 @@ __device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, f
     g.sync();
     for (int i = g.t; i < NX; i += NT) G[i * LDG + i] += 1.f;
     g.sync();
-    const bool ok = gj_solve<NX, NX, NT>(g, G, LDG);
+    const bool ok = gj_solve<NX, NX, NT>(g, G, LDG, scr + S::Wk);
     const float* XA = G + NX;
     mm<NX, NX, NX, true, false, NT, false>(g, out + E::P, NX, XA, LDG, U, NX, e1 + E::P, NX);
     mm<NX, 1, NX, true, false, NT, false>(g, out + E::p, 1, XA, LDG, w, 1, e1 + E::p, 1);
@@ -284,7 +286,7 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
                                            has_S ? st + L::S : nullptr, NX);
     mm<NU, 1, NX, true, false, NT, false>(g, Y + NX, LDY, st + L::B, NU, w, 1, st + L::r, 1);
     g.sync();
-    const bool ok = chol<NU, NT>(g, Gm, NU, dinv);
+    const bool ok = chol<NU, NT>(g, Gm, NU, dinv, scr + S::Wk);
     trsm_lower<NU, NX + 1, NT>(g, Gm, NU, dinv, Y, LDY);           // [Z | z]
     copy<NU, NX + 1, false, NT>(g, Y2, LDY, Y, LDY);
     trsm_lower_t<NU, NX + 1, NT>(g, Gm, NU, dinv, Y2, LDY);        // G^-1 [H | h]
@@ -336,19 +338,52 @@ __device__ void terminal_value(const Grp<NT>& g, const float* st, float* vout, c
 
 // Roll the trajectory of stages [k0, k1) forward from x (SMEM, length NX):
 // dx_k = x, du_k = K_k x + k_k, dlam_k = P_k x + p_k, x <- Abar_k x + bbar_k.
+// The per-stage operands are staged asynchronously, the next stage's while
+// the current one is used (two buffers of RollL::SIZE floats at buf).
+template <int NX, int NU>
+struct RollL {
+    static constexpr int K = 0, k = round4(NU * NX), P = round4(k + NU), p = round4(P + NX * NX),
+                         Ab = round4(p + NX), bb = round4(Ab + NX * NX), SIZE = round4(bb + NX);
+};
+
 template <int NX, int NU, int NT>
-__device__ void rollout_chunk(const Grp<NT>& g, float* x, float* xn, const KktArgs& a,
+__device__ __forceinline__ void roll_fetch(const Grp<NT>& g, float* b, const KktArgs& a, int64_t gs,
+                                           bool terminal)
+{
+    using L = RollL<NX, NU>;
+    stage_copy<NX * NX, NT, true>(g.t, b + L::P, a.P + gs * NX * NX);
+    stage_copy<NX, NT, true>(g.t, b + L::p, a.p + gs * NX);
+    if (!terminal) {
+        stage_copy<NU * NX, NT, true>(g.t, b + L::K, a.K + gs * NU * NX);
+        stage_copy<NU, NT, true>(g.t, b + L::k, a.k + gs * NU);
+        stage_copy<NX * NX, NT, true>(g.t, b + L::Ab, a.Abar + gs * NX * NX);
+        stage_copy<NX, NT, true>(g.t, b + L::bb, a.bbar + gs * NX);
+    }
+    cp_async_commit();
+}
+
+template <int NX, int NU, int NT>
+__device__ void rollout_chunk(const Grp<NT>& g, float* x, float* xn, float* buf, const KktArgs& a,
                               int64_t off, int N, int k0, int k1)
 {
+    using L = RollL<NX, NU>;
+    if (k0 >= k1) return;
+    roll_fetch<NX, NU, NT>(g, buf, a, off + k0, k0 == N);
     for (int k = k0; k < k1; ++k) {
         const int64_t gs = off + k;
+        float* cur = buf + ((k - k0) & 1) * L::SIZE;
+        if (k + 1 < k1) {
+            roll_fetch<NX, NU, NT>(g, buf + ((k + 1 - k0) & 1) * L::SIZE, a, gs + 1, k + 1 == N);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        g.sync();
         for (int i = g.t; i < NX; i += NT) a.dx[gs * NX + i] = x[i];
-        mv<NX, NX, false, NT, false>(g, a.dlam + gs * NX, a.P + gs * NX * NX, NX, x,
-                                     a.p + gs * NX);
+        mv<NX, NX, false, NT, false>(g, a.dlam + gs * NX, cur + L::P, NX, x, cur + L::p);
         if (k < N) {
-            mv<NU, NX, false, NT, false>(g, a.du + gs * NU, a.K + gs * NU * NX, NX, x,
-                                         a.k + gs * NU);
-            mv<NX, NX, false, NT, false>(g, xn, a.Abar + gs * NX * NX, NX, x, a.bbar + gs * NX);
+            mv<NU, NX, false, NT, false>(g, a.du + gs * NU, cur + L::K, NX, x, cur + L::k);
+            mv<NX, NX, false, NT, false>(g, xn, cur + L::Ab, NX, x, cur + L::bb);
             g.sync();
             for (int i = g.t; i < NX; i += NT) x[i] = xn[i];
         } else {
@@ -383,7 +418,9 @@ struct ScanSmem {
     // phase 1 (last chunk) / phase 3: stage | V0 | V1 | riccati scratch | Psi0 | Psi1 | psi
     static constexpr int PSI = round4(2 * ELEM + STG + RicL<NX, NU>::SIZE);
     static constexpr int P3 = PSI + 2 * NX * NX + round4(NX) * 2;
-    static constexpr int PRIV = round4(P1 > P3 ? P1 : P3);
+    static constexpr int P4 = 2 * round4(NX) + 2 * RollL<NX, NU>::SIZE;
+    static constexpr int PMAX = P1 > P3 ? P1 : P3;
+    static constexpr int PRIV = round4(PMAX > P4 ? PMAX : P4);
     static constexpr int SLOTS = W * ELEM;
     static constexpr int XS = W * round4(NX);
     static constexpr int TOTAL = SLOTS + W * PRIV + XS + 4;  // + status words
@@ -539,9 +576,10 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     if (active) {
         float* x = priv;                 // reuse the private area
         float* xn = priv + round4(NX);
+        float* rb = priv + 2 * round4(NX);
         for (int i = g.t; i < NX; i += 32) x[i] = xs[warp * round4(NX) + i];
         g.sync();
-        rollout_chunk<NX, NU, 32>(g, x, xn, a, off, N, k0, k1);
+        rollout_chunk<NX, NU, 32>(g, x, xn, rb, a, off, N, k0, k1);
     }
     __syncthreads();
     const int status = st_word[0];
@@ -549,8 +587,14 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     return status;
 }
 
+// CTAs per SM the register budget is sized for (128 registers per thread at most)
+template <int W>
+struct MinBlocks {
+    static constexpr int value = W >= 16 ? 1 : (W >= 8 ? 2 : (W >= 4 ? 4 : 16));
+};
+
 template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32) kkt_scan_kernel(KktArgs a)
+__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) kkt_scan_kernel(KktArgs a)
 {
     extern __shared__ __align__(16) float smem[];
     const int inst = a.order ? a.order[blockIdx.x] : blockIdx.x;
@@ -567,7 +611,8 @@ template <int NX, int NU>
 struct RicSmem {
     static constexpr int ELEM = ElemL<NX>::SIZE;
     static constexpr int STG = StageL<NX, NU>::SIZE;
-    static constexpr int TOTAL = STG + 2 * ELEM + RicL<NX, NU>::SIZE + 2 * round4(NX);
+    static constexpr int TOTAL = STG + 2 * ELEM + RicL<NX, NU>::SIZE + 2 * round4(NX) +
+                                 2 * RollL<NX, NU>::SIZE;
     static constexpr size_t BYTES = sizeof(float) * TOTAL;
 };
 
@@ -589,6 +634,7 @@ __global__ void __launch_bounds__(128) riccati_kernel(KktArgs a)
     float* scr = v1 + SM::ELEM;
     float* x = scr + RicL<NX, NU>::SIZE;
     float* xn = x + round4(NX);
+    float* rb = xn + round4(NX);
     const int N = a.N[inst];
     const int64_t off = a.off[inst];
     int bad = ST_OK;
@@ -603,7 +649,7 @@ __global__ void __launch_bounds__(128) riccati_kernel(KktArgs a)
     __threadfence_block();
     for (int i = g.t; i < NX; i += 32) x[i] = a.s[(int64_t)inst * NX + i];
     g.sync();
-    rollout_chunk<NX, NU, 32>(g, x, xn, a, off, N, 0, N + 1);
+    rollout_chunk<NX, NU, 32>(g, x, xn, rb, a, off, N, 0, N + 1);
     if (g.t == 0) a.status[inst] = bad;
 }
 

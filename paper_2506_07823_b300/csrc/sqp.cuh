@@ -38,7 +38,7 @@ struct SqpSmem {
 };
 
 template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32) sqp_kernel(SqpArgs a)
+__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) sqp_kernel(SqpArgs a)
 {
     using SM = SqpSmem<NX, NU, W>;
     extern __shared__ __align__(16) float smem[];

@@ -217,13 +217,38 @@ struct SrbdSource {
     const float *x, *u, *lam, *xref, *uref;
     const uint8_t* contact;
     int nrob;
+    // Inputs of stage gs (x_k, x_{k+1}, lam_k, lam_{k+1}, xref_k, u_k, uref_k,
+    // contact_k) are first copied into the stage's IN area asynchronously.
     template <int NX, int NU, int NT>
     __device__ __forceinline__ void load(const Grp<NT>& g, float* st, int64_t gs, bool terminal) const
     {
-        srbd_linearize_stage<NX, NU, NT>(
-            g, st, md, x + gs * NX, u + gs * NU, terminal ? nullptr : x + (gs + 1) * NX,
-            lam + gs * NX, terminal ? nullptr : lam + (gs + 1) * NX, xref + gs * NX,
-            uref + gs * NU, contact + gs * 4 * nrob, terminal);
+        using L = StageL<NX, NU>;
+        constexpr int SX = round4(NX), SU = round4(NU);
+        float* in = st + L::IN;
+        float* ix = in;
+        float* ix1 = in + SX;
+        float* il0 = in + 2 * SX;
+        float* il1 = in + 3 * SX;
+        float* ixr = in + 4 * SX;
+        float* iu = in + 5 * SX;
+        float* iur = iu + SU;
+        uint8_t* ict = reinterpret_cast<uint8_t*>(iur + SU);
+        stage_copy<NX, NT, true>(g.t, ix, x + gs * NX);
+        stage_copy<NX, NT, true>(g.t, il0, lam + gs * NX);
+        stage_copy<NX, NT, true>(g.t, ixr, xref + gs * NX);
+        if (!terminal) {
+            stage_copy<NX, NT, true>(g.t, ix1, x + (gs + 1) * NX);
+            stage_copy<NX, NT, true>(g.t, il1, lam + (gs + 1) * NX);
+            stage_copy<NU, NT, true>(g.t, iu, u + gs * NU);
+            stage_copy<NU, NT, true>(g.t, iur, uref + gs * NU);
+            // contact flags: nrob words of 4 bytes (4-byte aligned per stage)
+            const float* csrc = reinterpret_cast<const float*>(contact + gs * 4 * nrob);
+            for (int e = g.t; e < NX / 12; e += NT) cp_async4(reinterpret_cast<float*>(ict) + e, csrc + e);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        g.sync();
+        srbd_linearize_stage<NX, NU, NT>(g, st, md, ix, iu, ix1, il0, il1, ixr, iur, ict, terminal);
     }
     __device__ __forceinline__ bool has_S() const { return false; }
 };
