@@ -594,7 +594,7 @@ struct MinBlocks {
 };
 
 template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) kkt_scan_kernel(KktArgs a)
+__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) kkt_scan_kernel(const __grid_constant__ KktArgs a)
 {
     extern __shared__ __align__(16) float smem[];
     const int inst = a.order ? a.order[blockIdx.x] : blockIdx.x;
@@ -618,7 +618,7 @@ struct RicSmem {
 
 // One warp per instance; blockDim.x = 32 * warps-per-block.
 template <int NX, int NU>
-__global__ void __launch_bounds__(128) riccati_kernel(KktArgs a)
+__global__ void __launch_bounds__(128) riccati_kernel(const __grid_constant__ KktArgs a)
 {
     using SM = RicSmem<NX, NU>;
     extern __shared__ __align__(16) float smem[];

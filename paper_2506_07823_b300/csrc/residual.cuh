@@ -46,7 +46,7 @@ __device__ __forceinline__ double warp_max(double v)
 
 // One warp per stage slot; lanes own rows.
 template <int NX, int NU>
-__global__ void __launch_bounds__(256) kkt_residual_kernel(ResidArgs a)
+__global__ void __launch_bounds__(256) kkt_residual_kernel(const __grid_constant__ ResidArgs a)
 {
     const int64_t gs = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;

@@ -38,7 +38,7 @@ struct SqpSmem {
 };
 
 template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) sqp_kernel(SqpArgs a)
+__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) sqp_kernel(const __grid_constant__ SqpArgs a)
 {
     using SM = SqpSmem<NX, NU, W>;
     extern __shared__ __align__(16) float smem[];
@@ -149,7 +149,7 @@ struct LinArgs {
 
 // One warp per stage slot, four warps per block.
 template <int NX, int NU>
-__global__ void __launch_bounds__(128) linearize_kernel(LinArgs a)
+__global__ void __launch_bounds__(128) linearize_kernel(const __grid_constant__ LinArgs a)
 {
     using L = StageL<NX, NU>;
     extern __shared__ __align__(16) float smem[];
@@ -196,7 +196,7 @@ struct MeritArgs {
 };
 
 template <int NX, int NU>
-__global__ void __launch_bounds__(256) merit_kernel(MeritArgs a)
+__global__ void __launch_bounds__(256) merit_kernel(const __grid_constant__ MeritArgs a)
 {
     __shared__ double mer[32];
     const int inst = blockIdx.x;

@@ -213,7 +213,7 @@ __device__ void srbd_linearize_stage(const Grp<NT>& g, float* st, const pdilqr_s
 
 // Source of LQ stages that linearises the SRBD model on the fly.
 struct SrbdSource {
-    pdilqr_srbd_model md;
+    const pdilqr_srbd_model& md;   // kernel parameter space (grid constant)
     const float *x, *u, *lam, *xref, *uref;
     const uint8_t* contact;
     int nrob;
