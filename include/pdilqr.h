@@ -137,6 +137,39 @@ PDILQR_API pdilqr_status pdilqr_kkt_residual(pdilqr_plan *plan, const pdilqr_lq 
                                   const float *dx, const float *du, const float *dlam,
                                   double *resid, pdilqr_stream stream);
 
+/* --------------------------------------------- allocation-free scan solve */
+
+/* The LQ KKT scan solve of pdilqr_kkt_scan_solve for callers that may not
+ * allocate device memory at all -- a real-time control loop whose timing
+ * budget cannot absorb cudaMalloc (it can block and synchronise the device),
+ * code running while a CUDA graph is being captured (where cudaMalloc is not
+ * allowed), or a host application whose memory pool already owns the GPU.
+ * The paper has no counterpart: this is an interface of this library only.
+ *
+ * No plan is used and nothing is allocated: the per-stage workspace (policy,
+ * value function, closed-loop maps) lives in one static device array of
+ * 16 MiB that every GPU loading the library holds until the process exits.
+ * The caller passes inputs and outputs as in pdilqr_kkt_scan_solve, plus the
+ * batch tables as DEVICE arrays N [count] and stage_off [count] and the
+ * number of stage slots total_stages (>= max(stage_off + N + 1)); warps is
+ * 4, 8, 16 or 0 (= 8).  Batches needing more than
+ * pdilqr_noalloc_capacity_stages(n, m) stage slots are rejected with
+ * PDILQR_E_INVALID_ARG before any GPU work; an instance whose slots fall
+ * outside total_stages gets status PDILQR_E_INVALID_ARG and is skipped.  No
+ * refinement step.  The first call on a device looks up the array's device
+ * address (once per device); make that first call before any stream
+ * capture.  Every call shares the array: calls that overlap on the GPU race
+ * and must be serialised by the caller (one stream, or events).  No part of
+ * the array needs clearing between calls: every workspace slot a solve reads
+ * was written earlier in the same solve. */
+PDILQR_API pdilqr_status pdilqr_kkt_scan_solve_noalloc(
+    int32_t n, int32_t m, int32_t count, int64_t total_stages, const int32_t *N,
+    const int64_t *stage_off, int32_t warps, const pdilqr_lq *lq, const float *s, float *dx,
+    float *du, float *dlam, int32_t *status, pdilqr_stream stream);
+
+/* Stage slots that the static array holds for state / control sizes (n, m). */
+PDILQR_API int64_t pdilqr_noalloc_capacity_stages(int32_t n, int32_t m);
+
 /* ------------------------------------------------------ SRBD model, Sec. III */
 
 /* Single-rigid-body quadruped (the paper prints no equations; this is the

@@ -606,6 +606,28 @@ __global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) kkt_scan_kernel(c
 }
 
 
+// Scan solve for the allocation-free entry point: the batch tables come from
+// the caller, so every instance's slot range is checked against the scratch
+// capacity (limit stage slots) before any access; an instance that does not
+// fit is reported as invalid and skipped.
+template <int NX, int NU, int W>
+__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value)
+    kkt_scan_checked_kernel(const __grid_constant__ KktArgs a, int64_t limit)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int inst = blockIdx.x;
+    if (inst >= a.count) return;
+    const int N = a.N[inst];
+    const int64_t off = a.off[inst];
+    if (N < 1 || N > 4096 || off < 0 || off + N + 1 > limit) {
+        if (threadIdx.x == 0) a.status[inst] = 1;  // invalid argument
+        return;
+    }
+    const LqSource src(a);
+    const int st = scan_solve<NX, NU, W>(src, a, N, off, a.s + (int64_t)inst * NX, smem);
+    if (threadIdx.x == 0) a.status[inst] = st;
+}
+
 // --------------------------------------------------------- Riccati kernel
 template <int NX, int NU>
 struct RicSmem {

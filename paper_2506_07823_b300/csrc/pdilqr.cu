@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -56,6 +57,7 @@ struct SizeOps {
     cudaError_t (*merit)(const MeritArgs&, cudaStream_t);
     cudaError_t (*sqp)(const SqpArgs&, int warps, cudaStream_t);
     size_t (*sqp_smem)(int warps);
+    cudaError_t (*scan_checked)(const KktArgs&, int warps, int64_t limit, cudaStream_t);
 };
 
 template <int NX, int NU, int W>
@@ -73,6 +75,34 @@ static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
     }
     kkt_scan_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int NX, int NU, int W>
+static cudaError_t launch_scan_checked_w(const KktArgs& a, int64_t limit, cudaStream_t st)
+{
+    using SM = ScanSmem<NX, NU, W>;
+    if (SM::BYTES > kSmemMax) return cudaErrorInvalidConfiguration;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kkt_scan_checked_kernel<NX, NU, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SM::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kkt_scan_checked_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a, limit);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static cudaError_t launch_scan_checked(const KktArgs& a, int warps, int64_t limit, cudaStream_t st)
+{
+    switch (warps) {
+        case 4: return launch_scan_checked_w<NX, NU, 4>(a, limit, st);
+        case 8: return launch_scan_checked_w<NX, NU, 8>(a, limit, st);
+        case 16: return launch_scan_checked_w<NX, NU, 16>(a, limit, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int NX, int NU>
@@ -203,6 +233,7 @@ static SizeOps make_ops()
     o.riccati = launch_riccati<NX, NU>;
     o.resid = launch_resid<NX, NU>;
     o.scan_smem = scan_smem<NX, NU>;
+    o.scan_checked = launch_scan_checked<NX, NU>;
     if constexpr (SRBD) {
         o.linearize = launch_linearize<NX, NU>;
         o.merit = launch_merit<NX, NU>;
@@ -551,5 +582,81 @@ extern "C" pdilqr_status pdilqr_solve(pdilqr_plan* pl, const pdilqr_srbd_model* 
     a.J = info->J;
     a.theta = info->theta;
     PD_CUDA(pl->ops->sqp(a, pl->warps, (cudaStream_t)stream));
+    return PDILQR_OK;
+}
+
+// ------------------------------------------------ allocation-free scan solve
+// Scratch of pdilqr_kkt_scan_solve_noalloc: a file-scope device array that
+// every GPU loading this library holds until the process exits.  Host code
+// must not hand the array's name to a kernel (on the host it only stands in
+// for the symbol); the device address is looked up once per device.
+static constexpr size_t kNoAllocFloats = size_t(4) << 20;  // 16 MiB
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+static std::mutex g_noalloc_mu;
+static float* g_noalloc_addr[64] = {};
+
+static pdilqr_status noalloc_base(float** out)
+{
+    int dev = -1;
+    PD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return PDILQR_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return e != cudaSuccess ? cuda_status(e) : PDILQR_E_CUDA;
+        g_noalloc_addr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return PDILQR_OK;
+}
+
+extern "C" int64_t pdilqr_noalloc_capacity_stages(int32_t n, int32_t m)
+{
+    if (n < 1 || m < 1) return 0;
+    const size_t per = (size_t)m * n + m + 2 * (size_t)n * n + 2 * (size_t)n;
+    // six regions, each rounded up to 64 floats
+    return (int64_t)((kNoAllocFloats - 6 * 64) / per);
+}
+
+extern "C" pdilqr_status pdilqr_kkt_scan_solve_noalloc(
+    int32_t n, int32_t m, int32_t count, int64_t total_stages, const int32_t* N,
+    const int64_t* stage_off, int32_t warps, const pdilqr_lq* lq, const float* s, float* dx,
+    float* du, float* dlam, int32_t* status, pdilqr_stream stream)
+{
+    const SizeOps* ops = find_ops(n, m);
+    if (!ops || count < 1 || total_stages < 2 || !N || !stage_off || !lq_ok(lq) || !s || !dx ||
+        !du || !dlam || !status)
+        return PDILQR_E_INVALID_ARG;
+    if (total_stages > pdilqr_noalloc_capacity_stages(n, m)) return PDILQR_E_INVALID_ARG;
+    if (warps == 0) warps = 8;
+    if (warps != 4 && warps != 8 && warps != 16) return PDILQR_E_INVALID_ARG;
+    if (ops->scan_smem(warps) > kSmemMax) return PDILQR_E_INVALID_ARG;
+    float* base = nullptr;
+    pdilqr_status st = noalloc_base(&base);
+    if (st != PDILQR_OK) return st;
+    auto region = [&](size_t floats_per_stage) {
+        float* r = base;
+        base += (((size_t)total_stages * floats_per_stage) + 63) / 64 * 64;
+        return r;
+    };
+    KktArgs a;
+    a.A = lq->A; a.B = lq->B; a.c = lq->c; a.Q = lq->Q; a.R = lq->R; a.S = lq->S;
+    a.q = lq->q; a.r = lq->r;
+    a.s = s;
+    a.dx = dx; a.du = du; a.dlam = dlam;
+    a.K = region((size_t)m * n);
+    a.k = region((size_t)m);
+    a.P = region((size_t)n * n);
+    a.p = region((size_t)n);
+    a.Abar = region((size_t)n * n);
+    a.bbar = region((size_t)n);
+    a.N = N;
+    a.off = stage_off;
+    a.order = nullptr;
+    a.status = status;
+    a.count = count;
+    PD_CUDA(ops->scan_checked(a, warps, total_stages, (cudaStream_t)stream));
     return PDILQR_OK;
 }

@@ -122,6 +122,37 @@ _lib.pdilqr_solve.argtypes = [_vp, ctypes.POINTER(SrbdModel), ctypes.POINTER(_Sq
                               _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_SqpInfo), _vp]
 
 
+_lib.pdilqr_kkt_scan_solve_noalloc.argtypes = [
+    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_int32,
+    ctypes.POINTER(_LQ), _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.pdilqr_noalloc_capacity_stages.argtypes = [ctypes.c_int32, ctypes.c_int32]
+_lib.pdilqr_noalloc_capacity_stages.restype = ctypes.c_int64
+
+
+def noalloc_capacity_stages(n: int, m: int) -> int:
+    """Stage slots the static workspace of the allocation-free solve holds."""
+    return int(_lib.pdilqr_noalloc_capacity_stages(int(n), int(m)))
+
+
+def kkt_scan_solve_noalloc(n, m, N_dev, stage_off_dev, total_stages, lq: dict, s, dx, du, dlam,
+                           status, warps=0, stream=None):
+    """Allocation-free LQ KKT scan solve (pdilqr_kkt_scan_solve_noalloc).
+
+    For callers that must not allocate device memory (a real-time loop, a
+    stream being captured, a host whose pool owns the GPU): every array is
+    the caller's, the batch tables ``N_dev`` (int32) and ``stage_off_dev``
+    (int64) are device tensors, and the workspace is the library's static
+    device array.  Calls that overlap on the GPU race.
+    """
+    lqs = _LQ(*[_ptr(lq.get(k), name=k) if (k != "S" or lq.get("S") is not None) else None
+                for k in ("A", "B", "c", "Q", "R", "S", "q", "r")])
+    _check(_lib.pdilqr_kkt_scan_solve_noalloc(
+        int(n), int(m), int(N_dev.numel()), int(total_stages), _ptr(N_dev, torch.int32, "N"),
+        _ptr(stage_off_dev, torch.int64, "stage_off"), int(warps), ctypes.byref(lqs),
+        _ptr(s, name="s"), _ptr(dx, name="dx"), _ptr(du, name="du"), _ptr(dlam, name="dlam"),
+        _ptr(status, torch.int32, "status"), _stream(stream)), "pdilqr_kkt_scan_solve_noalloc")
+
+
 def lib() -> ctypes.CDLL:
     return _lib
 
