@@ -265,6 +265,80 @@ PDILQR_API pdilqr_status pdilqr_solve(pdilqr_plan *plan, const pdilqr_srbd_model
                                       const float *uref, const uint8_t *contact,
                                       pdilqr_sqp_info *info, pdilqr_stream stream);
 
+/* ------------------------------------------------------------ serving loop */
+
+/* A continuous-batching MPC server (the real-time iteration of Sec. II-F: one
+ * SQP iteration per control tick, warm-started from the previous solution
+ * shifted by one step).  Clients submit requests from host memory at any
+ * time; a dispatcher thread admits them into device slots, batches the
+ * requests whose clients are idle (grouped by state size), launches the fused
+ * SQP on one of several streams while other batches are still running, and
+ * completes tickets as their batch finishes.  Warm-start trajectories,
+ * multipliers and references stay resident on the device per client.
+ * Admission: a client's state is carved from a device pool of
+ * hbm_budget_bytes; when it does not fit the submit fails with
+ * PDILQR_E_ADMISSION.  All waits are bounded. */
+typedef struct {
+    int64_t hbm_budget_bytes;  /* device pool for client state (0: 1 GiB)         */
+    int32_t max_batch;         /* requests per launch (0: 1024; 1: one per launch)*/
+    int32_t max_inflight;      /* batches in flight on separate streams (0: 2)    */
+    int32_t max_N;             /* longest horizon a client may use (0: 100)       */
+    int32_t sqp_iters;         /* SQP iterations per request (0: 1)               */
+    int32_t warps;             /* warps per instance (0: 8; 1: sequential Riccati)*/
+    int32_t batch_window_us;   /* how long the dispatcher waits for more requests */
+                               /* once it has one and a stream is free (0: none)  */
+    pdilqr_srbd_model model;   /* robot and formation constants (shared by all    */
+                               /* clients); nrob is taken per client              */
+} pdilqr_serve_opts;
+
+typedef struct {
+    int32_t nrob;              /* robots of this client (n = m = 12 nrob); fixed  */
+    int32_t N;                 /* horizon of this client; fixed                   */
+    int32_t reset;             /* 1: re-initialise the warm start from x0hat      */
+    const float *x0hat;        /* HOST [n] measured state                         */
+    const float *xref;         /* HOST [N+1][n] or NULL (keep, shifted one step)  */
+    const float *uref;         /* HOST [N+1][m] or NULL (required with xref)      */
+    const uint8_t *contact;    /* HOST [N+1][nrob][4] or NULL (required with xref)*/
+} pdilqr_request;
+
+typedef struct {
+    int32_t status;            /* status of the solve                             */
+    int32_t iters;             /* SQP iterations run                              */
+    int64_t latency_ns;        /* submit to completion                            */
+    float *u0;                 /* caller's HOST [m] buffer for u_0, or NULL       */
+    float *x, *u;              /* caller's HOST [N+1][n], [N+1][m] buffers, or NULL */
+} pdilqr_result;
+
+typedef struct {
+    int64_t submitted, completed, refused, batches;
+    int64_t clients, pool_bytes_used, pool_bytes_total;
+    double mean_batch, p50_latency_us, p99_latency_us, solves_per_s;
+} pdilqr_serve_stats_t;
+
+typedef struct pdilqr_server pdilqr_server;
+
+/* Create a server on the current CUDA device (the pool is allocated here). */
+PDILQR_API pdilqr_status pdilqr_serve_create(const pdilqr_serve_opts *opts, pdilqr_server **out);
+/* Queue a request of client `client_id` (host data copied before return).  A
+ * new client is admitted here and must pass xref, uref and contact. */
+PDILQR_API pdilqr_status pdilqr_serve_submit(pdilqr_server *srv, uint64_t client_id,
+                                             const pdilqr_request *req, uint64_t *ticket);
+/* Wait up to timeout_us for a ticket; on success the ticket is consumed and
+ * the result copied to the caller's buffers; PDILQR_E_TIMEOUT otherwise. */
+PDILQR_API pdilqr_status pdilqr_serve_poll(pdilqr_server *srv, uint64_t ticket,
+                                           pdilqr_result *res, int64_t timeout_us);
+/* Free a client's device state (fails while it has a request in flight). */
+PDILQR_API pdilqr_status pdilqr_serve_release(pdilqr_server *srv, uint64_t client_id);
+/* Copy a client's warm start (x, u, lam in the trajectory layout, HOST) out,
+ * or back in; used to checkpoint and resume a controller. */
+PDILQR_API pdilqr_status pdilqr_serve_snapshot(pdilqr_server *srv, uint64_t client_id, float *x,
+                                               float *u, float *lam);
+PDILQR_API pdilqr_status pdilqr_serve_restore(pdilqr_server *srv, uint64_t client_id,
+                                              const float *x, const float *u, const float *lam);
+PDILQR_API pdilqr_status pdilqr_serve_stats(pdilqr_server *srv, pdilqr_serve_stats_t *out);
+/* Finish in-flight batches (bounded wait), free everything. */
+PDILQR_API pdilqr_status pdilqr_serve_destroy(pdilqr_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

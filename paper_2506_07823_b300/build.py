@@ -10,7 +10,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libpdilqr.so")
-SOURCES = ["pdilqr.cu"]
+SOURCES = ["pdilqr.cu", "serve.cu", "ops_small.cu", "ops_12.cu", "ops_24.cu", "ops_36.cu"]
+BUILD_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -27,18 +28,28 @@ def stale() -> bool:
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    if not force and not stale():
-        return LIB
-    nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
+def _compile(nvcc, src, obj, verbose):
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-fvisibility=hidden", "-shared", "-I" + INCLUDE,
-           "-o", tmp, *[os.path.join(CSRC, s) for s in SOURCES], "-lpthread"]
+           "-Xcompiler", "-fvisibility=hidden", "-I" + INCLUDE, "-c", "-o", obj, src]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)
+    return obj
+
+
+def build_library(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit (in parallel) and link libpdilqr.so."""
+    if not force and not stale():
+        return LIB
+    from concurrent.futures import ThreadPoolExecutor
+    nvcc = os.environ.get("NVCC", "nvcc")
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    jobs = [(os.path.join(CSRC, src), os.path.join(BUILD_DIR, src.replace(".cu", ".o")))
+            for src in SOURCES]
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(lambda j: _compile(nvcc, j[0], j[1], verbose), jobs))
+    tmp = LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

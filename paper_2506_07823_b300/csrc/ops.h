@@ -1,0 +1,34 @@
+// ops.h -- per-size kernel tables (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kkt_scan.cuh"
+#include "residual.cuh"
+#include "sqp.cuh"
+
+namespace pdl {
+
+static constexpr size_t kSmemMax = 227 * 1024;  // opt-in shared memory per CTA (sm_103a)
+
+struct SizeOps {
+    int n, m;
+    cudaError_t (*scan)(const KktArgs&, int warps, cudaStream_t);
+    cudaError_t (*riccati)(const KktArgs&, cudaStream_t);
+    cudaError_t (*resid)(const ResidArgs&, cudaStream_t);
+    size_t (*scan_smem)(int warps);
+    // SRBD model (n = m = 12 nrob); null for other sizes
+    cudaError_t (*linearize)(const LinArgs&, cudaStream_t);
+    cudaError_t (*merit)(const MeritArgs&, cudaStream_t);
+    cudaError_t (*sqp)(const SqpArgs&, int warps, cudaStream_t);
+    size_t (*sqp_smem)(int warps);
+    cudaError_t (*scan_checked)(const KktArgs&, int warps, int64_t limit, cudaStream_t);
+};
+
+// Tables of the instantiated sizes (one translation unit each).
+const SizeOps* ops_small(int n, int m);   // (1,1) (2,1) (3,2) (4,2)
+const SizeOps* ops_12(int n, int m);      // (12,12): SRBD, fused SQP
+const SizeOps* ops_24(int n, int m);      // (24,24): two stacked robots
+const SizeOps* ops_36(int n, int m);      // (36,24): Riccati comparator, residual
+
+}  // namespace pdl

@@ -1,0 +1,207 @@
+// ops_impl.cuh -- launch wrappers instantiated per (n, m) in the ops_*.cu units.
+// A kernel whose shared memory cannot fit on sm_103a is not instantiated; its
+// launcher reports cudaErrorInvalidConfiguration.
+#pragma once
+
+#include "ops.h"
+
+namespace pdl {
+
+
+template <int NX, int NU, int W>
+static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
+{
+    using SM = ScanSmem<NX, NU, W>;
+    if constexpr (SM::BYTES > kSmemMax) {
+        return cudaErrorInvalidConfiguration;
+    } else {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kkt_scan_kernel<NX, NU, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SM::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kkt_scan_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a);
+    return cudaGetLastError();
+    }
+}
+
+template <int NX, int NU, int W>
+static cudaError_t launch_scan_checked_w(const KktArgs& a, int64_t limit, cudaStream_t st)
+{
+    using SM = ScanSmem<NX, NU, W>;
+    if constexpr (SM::BYTES > kSmemMax) {
+        return cudaErrorInvalidConfiguration;
+    } else {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kkt_scan_checked_kernel<NX, NU, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SM::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kkt_scan_checked_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a, limit);
+    return cudaGetLastError();
+    }
+}
+
+template <int NX, int NU>
+static cudaError_t launch_scan_checked(const KktArgs& a, int warps, int64_t limit, cudaStream_t st)
+{
+    switch (warps) {
+        case 4: return launch_scan_checked_w<NX, NU, 4>(a, limit, st);
+        case 8: return launch_scan_checked_w<NX, NU, 8>(a, limit, st);
+        case 16: return launch_scan_checked_w<NX, NU, 16>(a, limit, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NX, int NU>
+static size_t scan_smem(int warps)
+{
+    switch (warps) {
+        case 1: return ScanSmem<NX, NU, 1>::BYTES;
+        case 4: return ScanSmem<NX, NU, 4>::BYTES;
+        case 8: return ScanSmem<NX, NU, 8>::BYTES;
+        case 16: return ScanSmem<NX, NU, 16>::BYTES;
+        default: return 0;
+    }
+}
+
+template <int NX, int NU>
+static cudaError_t launch_scan(const KktArgs& a, int warps, cudaStream_t st)
+{
+    switch (warps) {
+        case 1: return launch_scan_w<NX, NU, 1>(a, st);
+        case 4: return launch_scan_w<NX, NU, 4>(a, st);
+        case 8: return launch_scan_w<NX, NU, 8>(a, st);
+        case 16: return launch_scan_w<NX, NU, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NX, int NU>
+static cudaError_t launch_riccati(const KktArgs& a, cudaStream_t st)
+{
+    using SM = RicSmem<NX, NU>;
+    // warps (instances) per block: up to 4, as many as fit in shared memory
+    constexpr int FIT = (int)((227 * 1024) / SM::BYTES);
+    constexpr int WPB = FIT >= 4 ? 4 : (FIT >= 1 ? FIT : 1);
+    const size_t bytes = SM::BYTES * WPB;
+    if (bytes > kSmemMax) return cudaErrorInvalidConfiguration;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(riccati_kernel<NX, NU>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int grid = (a.count + WPB - 1) / WPB;
+    riccati_kernel<NX, NU><<<grid, 32 * WPB, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static cudaError_t launch_resid(const ResidArgs& a, cudaStream_t st)
+{
+    const int64_t blocks = (a.total_stages + 7) / 8;
+    kkt_residual_kernel<NX, NU><<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static cudaError_t launch_linearize(const LinArgs& a, cudaStream_t st)
+{
+    const size_t bytes = sizeof(float) * StageL<NX, NU>::SIZE * 4;
+    if (bytes > kSmemMax) return cudaErrorInvalidConfiguration;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(linearize_kernel<NX, NU>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t blocks = (a.total + 3) / 4;
+    linearize_kernel<NX, NU><<<(unsigned)blocks, 128, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU>
+static cudaError_t launch_merit(const MeritArgs& a, cudaStream_t st)
+{
+    merit_kernel<NX, NU><<<a.count, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NX, int NU, int W>
+static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
+{
+    using SM = SqpSmem<NX, NU, W>;
+    if constexpr (SM::BYTES > kSmemMax) {
+        return cudaErrorInvalidConfiguration;
+    } else {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sqp_kernel<NX, NU, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SM::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    sqp_kernel<NX, NU, W><<<a.ka.count, W * 32, SM::BYTES, st>>>(a);
+    return cudaGetLastError();
+    }
+}
+
+template <int NX, int NU>
+static cudaError_t launch_sqp(const SqpArgs& a, int warps, cudaStream_t st)
+{
+    switch (warps) {
+        case 1: return launch_sqp_w<NX, NU, 1>(a, st);
+        case 4: return launch_sqp_w<NX, NU, 4>(a, st);
+        case 8: return launch_sqp_w<NX, NU, 8>(a, st);
+        case 16: return launch_sqp_w<NX, NU, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NX, int NU>
+static size_t sqp_smem(int warps)
+{
+    switch (warps) {
+        case 1: return SqpSmem<NX, NU, 1>::BYTES;
+        case 4: return SqpSmem<NX, NU, 4>::BYTES;
+        case 8: return SqpSmem<NX, NU, 8>::BYTES;
+        case 16: return SqpSmem<NX, NU, 16>::BYTES;
+        default: return 0;
+    }
+}
+
+template <int NX, int NU, bool SRBD = false, bool FUSED = false>
+static SizeOps make_ops()
+{
+    SizeOps o{};
+    o.n = NX;
+    o.m = NU;
+    o.scan = launch_scan<NX, NU>;
+    o.riccati = launch_riccati<NX, NU>;
+    o.resid = launch_resid<NX, NU>;
+    o.scan_smem = scan_smem<NX, NU>;
+    o.scan_checked = launch_scan_checked<NX, NU>;
+    if constexpr (SRBD) {
+        o.linearize = launch_linearize<NX, NU>;
+        o.merit = launch_merit<NX, NU>;
+    }
+    if constexpr (FUSED) {
+        o.sqp = launch_sqp<NX, NU>;
+        o.sqp_smem = sqp_smem<NX, NU>;
+    }
+    return o;
+}
+
+
+}  // namespace pdl

@@ -7,9 +7,8 @@
 #include <new>
 #include <vector>
 
-#include "kkt_scan.cuh"
-#include "residual.cuh"
-#include "sqp.cuh"
+#include "ops.h"
+#include "plan.h"
 
 using namespace pdl;
 
@@ -43,251 +42,15 @@ static pdilqr_status cuda_status(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_status(e_);         \
     } while (0)
 
-// --------------------------------------------------------- per-size kernels
-static constexpr size_t kSmemMax = 227 * 1024;  // opt-in shared memory per CTA (sm_103a)
-
-struct SizeOps {
-    int n, m;
-    cudaError_t (*scan)(const KktArgs&, int warps, cudaStream_t);
-    cudaError_t (*riccati)(const KktArgs&, cudaStream_t);
-    cudaError_t (*resid)(const ResidArgs&, cudaStream_t);
-    size_t (*scan_smem)(int warps);
-    // SRBD model (n = m = 12 nrob); null for other sizes
-    cudaError_t (*linearize)(const LinArgs&, cudaStream_t);
-    cudaError_t (*merit)(const MeritArgs&, cudaStream_t);
-    cudaError_t (*sqp)(const SqpArgs&, int warps, cudaStream_t);
-    size_t (*sqp_smem)(int warps);
-    cudaError_t (*scan_checked)(const KktArgs&, int warps, int64_t limit, cudaStream_t);
-};
-
-template <int NX, int NU, int W>
-static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
-{
-    using SM = ScanSmem<NX, NU, W>;
-    if (SM::BYTES > kSmemMax) return cudaErrorInvalidConfiguration;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kkt_scan_kernel<NX, NU, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SM::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    kkt_scan_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int NX, int NU, int W>
-static cudaError_t launch_scan_checked_w(const KktArgs& a, int64_t limit, cudaStream_t st)
-{
-    using SM = ScanSmem<NX, NU, W>;
-    if (SM::BYTES > kSmemMax) return cudaErrorInvalidConfiguration;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kkt_scan_checked_kernel<NX, NU, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SM::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    kkt_scan_checked_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a, limit);
-    return cudaGetLastError();
-}
-
-template <int NX, int NU>
-static cudaError_t launch_scan_checked(const KktArgs& a, int warps, int64_t limit, cudaStream_t st)
-{
-    switch (warps) {
-        case 4: return launch_scan_checked_w<NX, NU, 4>(a, limit, st);
-        case 8: return launch_scan_checked_w<NX, NU, 8>(a, limit, st);
-        case 16: return launch_scan_checked_w<NX, NU, 16>(a, limit, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int NX, int NU>
-static size_t scan_smem(int warps)
-{
-    switch (warps) {
-        case 1: return ScanSmem<NX, NU, 1>::BYTES;
-        case 4: return ScanSmem<NX, NU, 4>::BYTES;
-        case 8: return ScanSmem<NX, NU, 8>::BYTES;
-        case 16: return ScanSmem<NX, NU, 16>::BYTES;
-        default: return 0;
-    }
-}
-
-template <int NX, int NU>
-static cudaError_t launch_scan(const KktArgs& a, int warps, cudaStream_t st)
-{
-    switch (warps) {
-        case 1: return launch_scan_w<NX, NU, 1>(a, st);
-        case 4: return launch_scan_w<NX, NU, 4>(a, st);
-        case 8: return launch_scan_w<NX, NU, 8>(a, st);
-        case 16: return launch_scan_w<NX, NU, 16>(a, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int NX, int NU>
-static cudaError_t launch_riccati(const KktArgs& a, cudaStream_t st)
-{
-    using SM = RicSmem<NX, NU>;
-    // warps (instances) per block: up to 4, as many as fit in shared memory
-    constexpr int FIT = (int)((227 * 1024) / SM::BYTES);
-    constexpr int WPB = FIT >= 4 ? 4 : (FIT >= 1 ? FIT : 1);
-    const size_t bytes = SM::BYTES * WPB;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(riccati_kernel<NX, NU>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)bytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int grid = (a.count + WPB - 1) / WPB;
-    riccati_kernel<NX, NU><<<grid, 32 * WPB, bytes, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int NX, int NU>
-static cudaError_t launch_resid(const ResidArgs& a, cudaStream_t st)
-{
-    const int64_t blocks = (a.total_stages + 7) / 8;
-    kkt_residual_kernel<NX, NU><<<(unsigned)blocks, 256, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int NX, int NU>
-static cudaError_t launch_linearize(const LinArgs& a, cudaStream_t st)
-{
-    const size_t bytes = sizeof(float) * StageL<NX, NU>::SIZE * 4;
-    if (bytes > kSmemMax) return cudaErrorInvalidConfiguration;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(linearize_kernel<NX, NU>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int64_t blocks = (a.total + 3) / 4;
-    linearize_kernel<NX, NU><<<(unsigned)blocks, 128, bytes, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int NX, int NU>
-static cudaError_t launch_merit(const MeritArgs& a, cudaStream_t st)
-{
-    merit_kernel<NX, NU><<<a.count, 256, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int NX, int NU, int W>
-static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
-{
-    using SM = SqpSmem<NX, NU, W>;
-    if (SM::BYTES > kSmemMax) return cudaErrorInvalidConfiguration;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sqp_kernel<NX, NU, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SM::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    sqp_kernel<NX, NU, W><<<a.ka.count, W * 32, SM::BYTES, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int NX, int NU>
-static cudaError_t launch_sqp(const SqpArgs& a, int warps, cudaStream_t st)
-{
-    switch (warps) {
-        case 1: return launch_sqp_w<NX, NU, 1>(a, st);
-        case 4: return launch_sqp_w<NX, NU, 4>(a, st);
-        case 8: return launch_sqp_w<NX, NU, 8>(a, st);
-        case 16: return launch_sqp_w<NX, NU, 16>(a, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int NX, int NU>
-static size_t sqp_smem(int warps)
-{
-    switch (warps) {
-        case 1: return SqpSmem<NX, NU, 1>::BYTES;
-        case 4: return SqpSmem<NX, NU, 4>::BYTES;
-        case 8: return SqpSmem<NX, NU, 8>::BYTES;
-        case 16: return SqpSmem<NX, NU, 16>::BYTES;
-        default: return 0;
-    }
-}
-
-template <int NX, int NU, bool SRBD = false, bool FUSED = false>
-static SizeOps make_ops()
-{
-    SizeOps o{};
-    o.n = NX;
-    o.m = NU;
-    o.scan = launch_scan<NX, NU>;
-    o.riccati = launch_riccati<NX, NU>;
-    o.resid = launch_resid<NX, NU>;
-    o.scan_smem = scan_smem<NX, NU>;
-    o.scan_checked = launch_scan_checked<NX, NU>;
-    if constexpr (SRBD) {
-        o.linearize = launch_linearize<NX, NU>;
-        o.merit = launch_merit<NX, NU>;
-    }
-    if constexpr (FUSED) {
-        o.sqp = launch_sqp<NX, NU>;
-        o.sqp_smem = sqp_smem<NX, NU>;
-    }
-    return o;
-}
-
 static const SizeOps* find_ops(int n, int m)
 {
-    static const SizeOps table[] = {
-        make_ops<1, 1>(), make_ops<2, 1>(), make_ops<3, 2>(), make_ops<4, 2>(),
-        make_ops<12, 12, true, true>(), make_ops<24, 24, true>(), make_ops<36, 24>(),
-    };
-    for (const auto& o : table)
-        if (o.n == n && o.m == m) return &o;
+    for (auto f : {ops_small, ops_12, ops_24, ops_36})
+        if (const SizeOps* o = f(n, m)) return o;
     return nullptr;
 }
 
 // -------------------------------------------------------------------- plan
-struct pdilqr_plan {
-    int n = 0, m = 0, count = 0, warps = 0, refine = 0, maxN = 0;
-    int64_t total = 0;
-    const SizeOps* ops = nullptr;
-    std::vector<void*> allocs;
-    int32_t* dN = nullptr;
-    int64_t* doff = nullptr;
-    int32_t* dorder = nullptr;
-    int64_t* dstage_inst = nullptr;
-    // policy / value function / closed-loop maps per stage
-    float *K = nullptr, *k = nullptr, *P = nullptr, *p = nullptr, *Abar = nullptr, *bbar = nullptr;
-    // refinement
-    float *rq = nullptr, *rr = nullptr, *rc = nullptr, *rs = nullptr;
-    float *ddx = nullptr, *ddu = nullptr, *ddl = nullptr, *dk = nullptr, *dp = nullptr;
-    double* norms = nullptr;
-    int32_t* st2 = nullptr;
 
-    template <typename T>
-    cudaError_t alloc(T** ptr, size_t count_) {
-        void* v = nullptr;
-        cudaError_t e = cudaMalloc(&v, std::max<size_t>(count_, 1) * sizeof(T));
-        if (e == cudaSuccess) {
-            allocs.push_back(v);
-            *ptr = static_cast<T*>(v);
-        }
-        return e;
-    }
-    ~pdilqr_plan() {
-        for (void* v : allocs) cudaFree(v);
-    }
-};
 
 static int pick_warps(const SizeOps* ops, int maxN)
 {
@@ -658,5 +421,59 @@ extern "C" pdilqr_status pdilqr_kkt_scan_solve_noalloc(
     a.status = status;
     a.count = count;
     PD_CUDA(ops->scan_checked(a, warps, total_stages, (cudaStream_t)stream));
+    return PDILQR_OK;
+}
+
+// ------------------------------------------------------------ capacity plans
+pdilqr_status pdl::plan_create_capacity(int n, int m, int max_count, int64_t slots, int warps,
+                                        pdilqr_plan** out)
+{
+    *out = nullptr;
+    const SizeOps* ops = find_ops(n, m);
+    if (!ops || max_count < 1 || slots < 2) return PDILQR_E_INVALID_ARG;
+    pdilqr_plan* pl = new (std::nothrow) pdilqr_plan();
+    if (!pl) return PDILQR_E_NO_MEMORY;
+    pl->n = n;
+    pl->m = m;
+    pl->ops = ops;
+    pl->count = 0;
+    pl->max_count = max_count;
+    pl->total = slots;
+    pl->warps = warps;
+    const size_t T = slots, C = max_count;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    chk(pl->alloc(&pl->dN, C));
+    chk(pl->alloc(&pl->doff, C));
+    chk(pl->alloc(&pl->dorder, C));
+    chk(pl->alloc(&pl->dstage_inst, T));
+    chk(pl->alloc(&pl->K, T * m * n));
+    chk(pl->alloc(&pl->k, T * m));
+    chk(pl->alloc(&pl->P, T * n * n));
+    chk(pl->alloc(&pl->p, T * n));
+    chk(pl->alloc(&pl->Abar, T * n * n));
+    chk(pl->alloc(&pl->bbar, T * n));
+    chk(pl->alloc(&pl->norms, C * 4));
+    chk(pl->alloc(&pl->st2, C));
+    chk(pl->alloc(&pl->ddx, T * n));
+    chk(pl->alloc(&pl->ddu, T * m));
+    chk(pl->alloc(&pl->ddl, T * n));
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_status(e);
+    }
+    *out = pl;
+    return PDILQR_OK;
+}
+
+pdilqr_status pdl::plan_set_batch_async(pdilqr_plan* pl, const int32_t* hN, const int64_t* hoff,
+                                        const int32_t* horder, int count, int maxN, cudaStream_t st)
+{
+    if (count < 1 || count > pl->max_count) return PDILQR_E_INVALID_ARG;
+    PD_CUDA(cudaMemcpyAsync(pl->dN, hN, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
+    PD_CUDA(cudaMemcpyAsync(pl->doff, hoff, sizeof(int64_t) * count, cudaMemcpyHostToDevice, st));
+    PD_CUDA(cudaMemcpyAsync(pl->dorder, horder, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
+    pl->count = count;
+    pl->maxN = maxN;
     return PDILQR_OK;
 }

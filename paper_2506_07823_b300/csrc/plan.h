@@ -1,0 +1,54 @@
+// plan.h -- the plan object behind pdilqr_plan (internal to the library).
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "ops.h"
+#include "pdilqr.h"
+
+struct pdilqr_plan {
+    int n = 0, m = 0, count = 0, warps = 0, refine = 0, maxN = 0;
+    int64_t total = 0;
+    const pdl::SizeOps* ops = nullptr;
+    std::vector<void*> allocs;
+    int32_t* dN = nullptr;
+    int64_t* doff = nullptr;
+    int32_t* dorder = nullptr;
+    int64_t* dstage_inst = nullptr;
+    // policy / value function / closed-loop maps per stage
+    float *K = nullptr, *k = nullptr, *P = nullptr, *p = nullptr, *Abar = nullptr, *bbar = nullptr;
+    // refinement
+    float *rq = nullptr, *rr = nullptr, *rc = nullptr, *rs = nullptr;
+    float *ddx = nullptr, *ddu = nullptr, *ddl = nullptr, *dk = nullptr, *dp = nullptr;
+    double* norms = nullptr;
+    int32_t* st2 = nullptr;
+    int max_count = 0;   // capacity of the batch tables (capacity plans)
+
+    template <typename T>
+    cudaError_t alloc(T** ptr, size_t count_) {
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, std::max<size_t>(count_, 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            allocs.push_back(v);
+            *ptr = static_cast<T*>(v);
+        }
+        return e;
+    }
+    ~pdilqr_plan() {
+        for (void* v : allocs) cudaFree(v);
+    }
+};
+
+namespace pdl {
+
+// A plan whose workspace holds `slots` stage slots and whose batch tables hold
+// up to `max_count` instances; the batch itself is set per launch.
+pdilqr_status plan_create_capacity(int n, int m, int max_count, int64_t slots, int warps,
+                                   pdilqr_plan** out);
+// Set the batch of a capacity plan from host arrays (pinned for asynchronous
+// copies): horizons, first slots and CTA order.  Stream-ordered.
+pdilqr_status plan_set_batch_async(pdilqr_plan* pl, const int32_t* hN, const int64_t* hoff,
+                                   const int32_t* horder, int count, int maxN, cudaStream_t st);
+
+}  // namespace pdl

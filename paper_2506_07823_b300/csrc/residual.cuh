@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) kkt_residual_kernel(const __grid_constant
 }
 
 // z += dz over n elements (one refinement update).
-__global__ void axpy_kernel(float* __restrict__ z, const float* __restrict__ dz, int64_t n)
+static __global__ void axpy_kernel(float* __restrict__ z, const float* __restrict__ dz, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) z[i] += dz[i];

@@ -318,6 +318,121 @@ class Plan:
         return info
 
 
+# ------------------------------------------------------------------ serving
+class _ServeOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("max_N", ctypes.c_int32),
+                ("sqp_iters", ctypes.c_int32), ("warps", ctypes.c_int32),
+                ("batch_window_us", ctypes.c_int32), ("model", SrbdModel)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("nrob", ctypes.c_int32), ("N", ctypes.c_int32), ("reset", ctypes.c_int32),
+                ("x0hat", _vp), ("xref", _vp), ("uref", _vp), ("contact", _vp)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("latency_ns", ctypes.c_int64), ("u0", _vp), ("x", _vp), ("u", _vp)]
+
+
+class _ServeStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "refused", "batches",
+                                              "clients", "pool_bytes_used", "pool_bytes_total")] + \
+               [(k, ctypes.c_double) for k in ("mean_batch", "p50_latency_us", "p99_latency_us",
+                                               "solves_per_s")]
+
+
+_lib.pdilqr_serve_create.argtypes = [ctypes.POINTER(_ServeOpts), ctypes.POINTER(_vp)]
+_lib.pdilqr_serve_submit.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(_Request),
+                                     ctypes.POINTER(ctypes.c_uint64)]
+_lib.pdilqr_serve_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(_Result), ctypes.c_int64]
+_lib.pdilqr_serve_release.argtypes = [_vp, ctypes.c_uint64]
+_lib.pdilqr_serve_snapshot.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _vp]
+_lib.pdilqr_serve_restore.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _vp]
+_lib.pdilqr_serve_stats.argtypes = [_vp, ctypes.POINTER(_ServeStats)]
+_lib.pdilqr_serve_destroy.argtypes = [_vp]
+
+
+def _hptr(a, dtype):
+    """Host pointer of a contiguous numpy array of ``dtype`` (kept alive by the caller)."""
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+class Server:
+    """Continuous-batching MPC server (pdilqr_serve_*) on the current device."""
+
+    def __init__(self, model_params: dict, hbm_budget_bytes: int = 1 << 30, max_batch: int = 1024,
+                 max_inflight: int = 2, max_N: int = 100, sqp_iters: int = 1, warps: int = 8,
+                 batch_window_us: int = 0):
+        o = _ServeOpts(int(hbm_budget_bytes), int(max_batch), int(max_inflight), int(max_N),
+                       int(sqp_iters), int(warps), int(batch_window_us), srbd_model(model_params))
+        h = _vp()
+        _check(_lib.pdilqr_serve_create(ctypes.byref(o), ctypes.byref(h)), "pdilqr_serve_create")
+        self._h = h
+
+    def submit(self, client: int, nrob: int, N: int, x0hat, xref=None, uref=None, contact=None,
+               reset: bool = False) -> int:
+        keep = [_hptr(x0hat, np.float32), _hptr(xref, np.float32), _hptr(uref, np.float32),
+                _hptr(contact, np.uint8)]
+        q = _Request(int(nrob), int(N), int(bool(reset)), *[k[1] for k in keep])
+        t = ctypes.c_uint64()
+        _check(_lib.pdilqr_serve_submit(self._h, ctypes.c_uint64(client), ctypes.byref(q),
+                                        ctypes.byref(t)), "pdilqr_serve_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_us: int = 10_000_000, n: int | None = None,
+             N: int | None = None) -> dict:
+        """Wait for a ticket.  With ``n`` and ``N`` the trajectories are returned."""
+        out = {}
+        bufs = {}
+        if n is not None:
+            bufs["u0"] = np.zeros(n, np.float32)
+            if N is not None:
+                bufs["x"] = np.zeros((N + 1, n), np.float32)
+                bufs["u"] = np.zeros((N + 1, n), np.float32)
+        r = _Result(0, 0, 0, *[bufs[k].ctypes.data if k in bufs else None for k in ("u0", "x", "u")])
+        _check(_lib.pdilqr_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(r),
+                                      int(timeout_us)), "pdilqr_serve_poll")
+        out.update(status=r.status, iters=r.iters, latency_us=r.latency_ns / 1e3, **bufs)
+        return out
+
+    def release(self, client: int):
+        _check(_lib.pdilqr_serve_release(self._h, ctypes.c_uint64(client)), "pdilqr_serve_release")
+
+    def snapshot(self, client: int, n: int, N: int):
+        x = np.zeros((N + 1, n), np.float32)
+        u = np.zeros((N + 1, n), np.float32)
+        lam = np.zeros((N + 1, n), np.float32)
+        _check(_lib.pdilqr_serve_snapshot(self._h, ctypes.c_uint64(client), x.ctypes.data,
+                                          u.ctypes.data, lam.ctypes.data), "pdilqr_serve_snapshot")
+        return x, u, lam
+
+    def restore(self, client: int, x, u, lam):
+        k = [_hptr(v, np.float32) for v in (x, u, lam)]
+        _check(_lib.pdilqr_serve_restore(self._h, ctypes.c_uint64(client), *[v[1] for v in k]),
+               "pdilqr_serve_restore")
+
+    def stats(self) -> dict:
+        st = _ServeStats()
+        _check(_lib.pdilqr_serve_stats(self._h, ctypes.byref(st)), "pdilqr_serve_stats")
+        return {k: getattr(st, k) for k, _ in _ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pdilqr_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def backward_error(resid: torch.Tensor) -> torch.Tensor:
     """Normwise backward error |Kz - rhs| / (|K| |z| + |rhs|) per instance."""
     r = resid.double()

@@ -90,12 +90,14 @@ def check_parity(insts, Nv, off, out, s, with_S, policy=False):
 
 @pytest.mark.parametrize("solver", ["scan", "riccati"])
 @pytest.mark.parametrize("warps", [4, 8, 16])
-@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (3, 2), (4, 2), (12, 12)])
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (3, 2), (4, 2), (12, 12), (24, 24)])
 def test_ltv_parity_ragged(solver, warps, n, m):
     """Uneven horizons in one batch: N = 1 (degenerate), tiny, and spanning
     several chunks with a ragged tail."""
     if solver == "riccati" and warps != 4:
         pytest.skip("warp count only affects the scan")
+    if n == 24 and warps != 4:
+        pytest.skip("n = 24 fits shared memory with 4 warps per instance only")
     Ns = [1, 2, 3, 5, 16, 17, 50, 100]
     insts, packed, Nv, off, s = make_batch(n, m, Ns, seed=100 * n + m)
     from paper_2506_07823_b300.pdilqr import Plan
