@@ -301,6 +301,15 @@ def run_gpu(args):
         except Exception:
             traffic = None
         extras = measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args)
+        serving = None
+        if args.serve_seconds > 0:
+            serving = {
+                "workload": "Poisson arrivals, one real-time SQP iteration per request, N = 50, "
+                            "256 clients: one robot (n = 12) or two robots (n = 24)",
+                "continuous_batching_scan": measure_serving(pdilqr, args, args.serve_seconds,
+                                                            args.serve_rate, 1024, 8, 2),
+                "one_request_per_launch_riccati": measure_serving(pdilqr, args, args.serve_seconds,
+                                                                  args.serve_rate, 1, 1, 1)}
         e2e = measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args)
         cpu = None
         if pool is not None:
@@ -323,6 +332,7 @@ def run_gpu(args):
             "latency_ms": {"batch_p50": pct(times, 50), "batch_p99": pct(times, 99),
                            **extras["latency"]},
             "comparators": extras["comparators"],
+            "serving": serving,
             "status_counts": {str(int(s)): int((st == s).sum()) for s in np.unique(st)},
             "kkt_solves_per_step": kkt_all,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
@@ -462,6 +472,76 @@ def measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.mean(t))}
 
 
+def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, warps: int,
+                    inflight: int, seed: int = 0):
+    """Poisson arrivals at ``rate`` requests/s for ``seconds``: each request is
+    one real-time SQP iteration of a client's MPC problem (N = 50; half the
+    clients one robot, half two robots coupled by the formation cost).
+    Returns achieved solves/s, latency percentiles and the mean batch size."""
+    import threading
+    prm = synth.srbd_params(2)
+    srv = pdilqr.Server(prm, hbm_budget_bytes=1 << 30, max_batch=max_batch, max_inflight=inflight,
+                        max_N=50, sqp_iters=1, warps=warps)
+    n_clients = 256
+    probs = {c: synth.srbd_problem(50, seed=10_000 + c, nrob=1 + (c % 2)) for c in range(n_clients)}
+    g = np.random.default_rng(seed)
+    gaps = g.exponential(1.0 / rate, size=int(rate * seconds * 1.2) + 16)
+    picks = g.integers(0, n_clients, size=gaps.size)
+    tickets = []
+    lat = []
+    done = threading.Event()
+    lock = threading.Lock()
+
+    def collector():
+        i = 0
+        while True:
+            with lock:
+                have = i < len(tickets)
+                tk = tickets[i] if have else None
+            if not have:
+                if done.is_set():
+                    with lock:
+                        if i >= len(tickets):
+                            return
+                    continue
+                time.sleep(0.0002)
+                continue
+            r = srv.poll(tk, timeout_us=60_000_000)
+            lat.append(r["latency_us"])
+            i += 1
+
+    th = threading.Thread(target=collector, daemon=True)
+    # admit every client once (untimed)
+    for c in range(n_clients):
+        p = probs[c]
+        srv.poll(srv.submit(c, p["nrob"], 50, p["x0hat"], p["xref"], p["uref"], p["contact"]))
+    th.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    k = 0
+    while t_next - t0 < seconds and k < gaps.size:
+        now = time.perf_counter()
+        if now < t_next:
+            time.sleep(min(t_next - now, 0.001))
+            continue
+        c = int(picks[k])
+        p = probs[c]
+        tk = srv.submit(c, p["nrob"], 50, p["x0hat"], p["xref"], p["uref"], p["contact"])
+        with lock:
+            tickets.append(tk)
+        t_next += gaps[k]
+        k += 1
+    done.set()
+    th.join(timeout=120)
+    t1 = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    return {"offered_per_s": rate, "requests": k, "solves_per_s": len(lat) / (t1 - t0),
+            "p50_ms": pct(lat, 50) / 1e3, "p99_ms": pct(lat, 99) / 1e3,
+            "mean_batch": st["mean_batch"], "max_batch": max_batch, "warps": warps,
+            "streams": inflight}
+
+
 # --------------------------------------------------------- reference arm
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -506,6 +586,9 @@ def main():
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--comparator-sample", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="duration of each serving scenario (0 skips them)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (1/s)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
