@@ -68,26 +68,26 @@ struct ElemL {  // CVF element (A, C, b, P, p); a value function uses P, p only,
                          p = 3 * NX * NX + NX, SIZE = round4(3 * NX * NX + 2 * NX);
 };
 
-// (Wk: small scratch of the one-warp factorisations, 2 (dim + 3) floats)
+// (Wk: small scratch of the one-warp factorisations, 3 (dim + 1) floats)
 template <int NX, int NU>
 struct BuildL {  // scratch of the element build
     static constexpr int Lr = 0, dinv = Lr + NU * NU, Z = round4(dinv + NU),
                          Y = Z + NU * NX, Wk = round4(Y + NU * (NX + 1)),
-                         SIZE = round4(Wk + 2 * (NU + 3));
+                         SIZE = round4(Wk + 3 * (NU + 1));
 };
 
 template <int NX>
 struct CombL {  // scratch of a combine
     static constexpr int LDG = 3 * NX + 1;
     static constexpr int G = 0, T = round4(NX * LDG), U = T + NX * NX, w = U + NX * NX,
-                         Wk = round4(w + NX), SIZE = round4(Wk + 2 * (NX + 3));
+                         Wk = round4(w + NX), SIZE = round4(Wk + 3 * (NX + 1));
 };
 
 template <int NX, int NU>
 struct RicL {  // scratch of one Riccati step
     static constexpr int PB = 0, PA = PB + NX * NU, w = PA + NX * NX, G = round4(w + NX),
                          dinv = G + NU * NU, Y = round4(dinv + NU), Y2 = Y + NU * (NX + 1),
-                         Wk = round4(Y2 + NU * (NX + 1)), SIZE = round4(Wk + 2 * (NU + 3));
+                         Wk = round4(Y2 + NU * (NX + 1)), SIZE = round4(Wk + 3 * (NU + 1));
 };
 
 // ------------------------------------------------------------ stage loading
@@ -123,6 +123,14 @@ struct LqSource {
         KktArgs t;
         t.A = A; t.B = B; t.c = c; t.Q = Q; t.R = R; t.S = S; t.q = q; t.r = r;
         load_stage<NX, NU, NT>(g, st, t, gs, terminal);
+    }
+    // the caller's arrays are read again in the Riccati sweep: nothing to keep
+    template <int NX, int NU, int NT>
+    __device__ __forceinline__ void keep(const Grp<NT>&, const float*, int64_t) const {}
+    template <int NX, int NU, int NT>
+    __device__ __forceinline__ void reload(const Grp<NT>& g, float* st, int64_t gs) const
+    {
+        load<NX, NU, NT>(g, st, gs, false);
     }
     __device__ __forceinline__ bool has_S() const { return S != nullptr; }
 };
@@ -466,6 +474,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         float* other = tmpE;
         for (int k = k0; k < k1; ++k) {
             src.template load<NX, NU, 32>(g, stg, off + k, false);
+            src.template keep<NX, NU, 32>(g, stg, off + k);
             if (k == k0) {
                 if (!build_element<NX, NU, 32>(g, stg, acc, scr, has_S, false)) bad = ST_NOT_SPD;
             } else {
@@ -541,7 +550,8 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         g.sync();
         for (int k = k1 - 1; k >= k0; --k) {
             const int64_t gs = off + k;
-            src.template load<NX, NU, 32>(g, stg, gs, false);
+            if (warp > 0) src.template reload<NX, NU, 32>(g, stg, gs);   // kept in phase 1
+            else src.template load<NX, NU, 32>(g, stg, gs, false);
             if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, gs, has_S)) bad = ST_NOT_SPD;
             float* t = v0; v0 = v1; v1 = t;
             __threadfence_block();

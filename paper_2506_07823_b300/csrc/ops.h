@@ -23,6 +23,7 @@ struct SizeOps {
     cudaError_t (*sqp)(const SqpArgs&, int warps, cudaStream_t);
     size_t (*sqp_smem)(int warps);
     cudaError_t (*scan_checked)(const KktArgs&, int warps, int64_t limit, cudaStream_t);
+    int lq_stage_floats;   // floats of one linearised stage kept by the fused SQP
 };
 
 // Tables of the instantiated sizes (one translation unit each).

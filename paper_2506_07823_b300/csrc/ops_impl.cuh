@@ -192,6 +192,7 @@ static SizeOps make_ops()
     o.resid = launch_resid<NX, NU>;
     o.scan_smem = scan_smem<NX, NU>;
     o.scan_checked = launch_scan_checked<NX, NU>;
+    o.lq_stage_floats = StageL<NX, NU>::IN;
     if constexpr (SRBD) {
         o.linearize = launch_linearize<NX, NU>;
         o.merit = launch_merit<NX, NU>;

@@ -113,6 +113,7 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
     PD_CUDA(pl->alloc(&pl->ddx, T * n));
     PD_CUDA(pl->alloc(&pl->ddu, T * m));
     PD_CUDA(pl->alloc(&pl->ddl, T * n));
+    if (pl->ops->sqp) PD_CUDA(pl->alloc(&pl->lqcache, T * (size_t)pl->ops->lq_stage_floats));
     PD_CUDA(cudaMemcpy(pl->dN, hN.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(pl->doff, hoff.data(), C * sizeof(int64_t), cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(pl->dorder, order.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -344,6 +345,7 @@ extern "C" pdilqr_status pdilqr_solve(pdilqr_plan* pl, const pdilqr_srbd_model* 
     a.alpha = info->alpha;
     a.J = info->J;
     a.theta = info->theta;
+    a.lqcache = pl->lqcache;
     PD_CUDA(pl->ops->sqp(a, pl->warps, (cudaStream_t)stream));
     return PDILQR_OK;
 }
@@ -458,6 +460,7 @@ pdilqr_status pdl::plan_create_capacity(int n, int m, int max_count, int64_t slo
     chk(pl->alloc(&pl->ddx, T * n));
     chk(pl->alloc(&pl->ddu, T * m));
     chk(pl->alloc(&pl->ddl, T * n));
+    if (ops->sqp) chk(pl->alloc(&pl->lqcache, T * (size_t)ops->lq_stage_floats));
     if (e != cudaSuccess) {
         delete pl;
         return cuda_status(e);

@@ -23,6 +23,7 @@ struct pdilqr_plan {
     float *ddx = nullptr, *ddu = nullptr, *ddl = nullptr, *dk = nullptr, *dp = nullptr;
     double* norms = nullptr;
     int32_t* st2 = nullptr;
+    float* lqcache = nullptr;   // linearised stages kept by the fused SQP (SRBD sizes)
     int max_count = 0;   // capacity of the batch tables (capacity plans)
 
     template <typename T>

@@ -25,6 +25,7 @@ struct SqpArgs {
     int32_t *iters, *status;        // [count]
     float* alpha;                   // [count][max_iters] or null
     double *J, *theta;              // [count] or null
+    float* lqcache;                 // [slots][StageL::IN] linearised-stage cache or null
 };
 
 template <int NX, int NU, int W>
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) sqp_kernel(const 
     float* alpha_sh = smem + SM::CTL;
     int* ctl = reinterpret_cast<int*>(smem + SM::CTL + 1);    // [0] converged flag
 
-    const SrbdSource src{a.md, a.x, a.u, a.lam, a.xref, a.uref, a.contact, nrob};
+    const SrbdSource src{a.md, a.x, a.u, a.lam, a.xref, a.uref, a.contact, nrob, a.lqcache};
     const float* xh = a.x0hat + (int64_t)inst * NX;
     float* x = a.x + off * NX;
     float* u = a.u + off * NU;

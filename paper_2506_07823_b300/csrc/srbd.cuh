@@ -101,6 +101,36 @@ __device__ __forceinline__ void srbd_xdot(const pdilqr_srbd_model& md, const flo
     }
 }
 
+// Component r of the time derivative of one robot's state.
+__device__ __forceinline__ float srbd_xdot_comp(const pdilqr_srbd_model& md, const float* x,
+                                                const float* u, const uint8_t* s, int r)
+{
+    if (r < 3) return x[6 + r];
+    if (r < 6) return x[9 + (r - 3)];
+    if (r < 9) {
+        const int a = r - 6;
+        float fs = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (s[j]) fs += u[3 * j + a];
+        return fs / md.mass - (a == 2 ? md.gravity : 0.f);
+    }
+    const int a = r - 9, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    const float* p = x;
+    const float* w = x + 9;
+    float tau = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (!s[j]) continue;
+        const float* f = u + 3 * j;
+        // ((foot_j - p) x f)_a
+        tau += (md.foot[j][a1] - p[a1]) * f[a2] - (md.foot[j][a2] - p[a2]) * f[a1];
+    }
+    // (w x I w)_a
+    const float gyro = w[a1] * md.inertia[a2] * w[a2] - w[a2] * md.inertia[a1] * w[a1];
+    return (tau - gyro) / md.inertia[a];
+}
+
 // ------------------------------------------------------ stage linearisation
 // Writes one stage in the StageL layout: A, B, c, Q, R, q, r (S = 0 is not
 // written).  x1, l1 (next state / costate) are not read at the terminal.
@@ -116,8 +146,12 @@ __device__ void srbd_linearize_stage(const Grp<NT>& g, float* st, const pdilqr_s
     const float dt = md.dt;
     const float* Wx = terminal ? md.WN : md.W;
     const bool form = NR > 1;
+    // state rows and control rows run on disjoint lanes of a warp
+    constexpr int HALF = (NT == 32) ? 16 : NT;
+    const int ts = (NT == 32) ? (g.t < 16 ? g.t : NX) : g.t;        // state-row lane
+    const int tc = (NT == 32) ? (g.t >= 16 ? g.t - 16 : NU) : g.t;  // control-row lane
     // ---- state rows: A, B, c, Q, cost gradient in q
-    for (int i = g.t; i < NX; i += NT) {
+    for (int i = ts; i < NX; i += HALF) {
         const int b = i / 12, r = i % 12, o = 12 * b;
         const float* xb = x + o;
         float* Arow = st + L::A + i * NX;
@@ -142,9 +176,7 @@ __device__ void srbd_linearize_stage(const Grp<NT>& g, float* st, const pdilqr_s
         for (int j = 0; j < NX; ++j) Arow[j] = 0.f;
         for (int j = 0; j < NU; ++j) Brow[j] = 0.f;
         Arow[i] = 1.f;
-        float xd[12];
-        srbd_xdot(md, xb, ub, sb, xd);
-        st[L::c + i] = (xb[r] - x1[i]) + dt * xd[r];   // difference first: no rounding of h
+        st[L::c + i] = (xb[r] - x1[i]) + dt * srbd_xdot_comp(md, xb, ub, sb, r);  // difference first
         if (r < 3) {
             Arow[o + 6 + r] = dt;
         } else if (r < 6) {
@@ -178,7 +210,7 @@ __device__ void srbd_linearize_stage(const Grp<NT>& g, float* st, const pdilqr_s
     }
     // ---- control rows: R, cost gradient in r
     if (!terminal) {
-        for (int i = g.t; i < NU; i += NT) {
+        for (int i = tc; i < NU; i += HALF) {
             const int b = i / 12, r = i % 12, o = 12 * b, j = r / 3, comp = r % 3;
             float* Rrow = st + L::R + i * NU;
             for (int l = 0; l < NU; ++l) Rrow[l] = 0.f;
@@ -217,6 +249,32 @@ struct SrbdSource {
     const float *x, *u, *lam, *xref, *uref;
     const uint8_t* contact;
     int nrob;
+    float* cache;                  // per-slot copy of linearised stages (or null)
+
+    // Keep a linearised stage (the LQ blocks, StageL::IN floats) so that the
+    // Riccati sweep can stream it back instead of linearising again.
+    template <int NX, int NU, int NT>
+    __device__ __forceinline__ void keep(const Grp<NT>& g, const float* st, int64_t gs) const
+    {
+        constexpr int F = StageL<NX, NU>::IN;
+        if (!cache) return;
+        float4* dst = reinterpret_cast<float4*>(cache + gs * F);
+        const float4* src = reinterpret_cast<const float4*>(st);
+        for (int e = g.t; e < F / 4; e += NT) dst[e] = src[e];
+    }
+    template <int NX, int NU, int NT>
+    __device__ __forceinline__ void reload(const Grp<NT>& g, float* st, int64_t gs) const
+    {
+        constexpr int F = StageL<NX, NU>::IN;
+        if (!cache) {
+            load<NX, NU, NT>(g, st, gs, false);
+            return;
+        }
+        stage_copy<F, NT, true>(g.t, st, cache + gs * F);
+        cp_async_commit();
+        cp_async_wait_all();
+        g.sync();
+    }
     // Inputs of stage gs (x_k, x_{k+1}, lam_k, lam_{k+1}, xref_k, u_k, uref_k,
     // contact_k) are first copied into the stage's IN area asynchronously.
     template <int NX, int NU, int NT>
