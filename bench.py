@@ -167,6 +167,28 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------- multi-rank
+def rank_seed(rank: int, count: int) -> int:
+    """Replicas: rank r solves its own batch of ``count`` instances drawn from
+    the Philox streams seed + r * count .. seed + (r + 1) * count - 1."""
+    return SEED + rank * count
+
+
+def aggregate(ms_local: float, kkt_local: float, device) -> tuple[float, float]:
+    """Whole-job step time (max over ranks) and KKT solves (sum over ranks).
+    Works with any torch.distributed backend (gloo on CPU tensors, nccl on
+    CUDA tensors); a single process returns its own numbers."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, kkt_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    k = torch.tensor([kkt_local], dtype=torch.float64, device=device)
+    dist.all_reduce(k, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(k.item())
+
+
 # ---------------------------------------------------------------- GPU arm
 def build_device_batch(torch, insts, packed, Nv, off, x0, dev):
     t = {}
@@ -215,7 +237,7 @@ def run_gpu(args):
     cores = host_cores()
     pool = oracle_pool(cores) if (rank == 0 and not args.no_cpu) else None
 
-    insts, packed, Nv, off, x0 = synth.srbd_batch(args.count, seed=SEED + rank * args.count,
+    insts, packed, Nv, off, x0 = synth.srbd_batch(args.count, seed=rank_seed(rank, args.count),
                                                   Ns_choices=HORIZONS)
     total_stages = int(Nv.sum() + len(Nv))
     prm = synth.srbd_params()
@@ -277,16 +299,7 @@ def run_gpu(args):
     clk = clocks.stop()
     kkt_per_step = int(info["iters"].sum().item())
     st = info["status"].cpu().numpy()
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        k = torch.tensor([kkt_per_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(k)
-        kkt_all = float(k.item())
-    else:
-        kkt_all = float(kkt_per_step)
+    ms, kkt_all = aggregate(float(np.mean(times)), float(kkt_per_step), dev)
     value = kkt_all / (ms / 1e3)
 
     result = None
