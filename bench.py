@@ -314,6 +314,7 @@ def run_gpu(args):
         except Exception:
             traffic = None
         extras = measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args)
+        lqw = measure_lq_workloads(torch, pdilqr, dev, stream, args) if args.lq_workloads else None
         serving = None
         if args.serve_seconds > 0:
             serving = {
@@ -346,6 +347,7 @@ def run_gpu(args):
                            **extras["latency"]},
             "comparators": extras["comparators"],
             "serving": serving,
+            "lq_workloads": lqw,
             "status_counts": {str(int(s)): int((st == s).sum()) for s in np.unique(st)},
             "kkt_solves_per_step": kkt_all,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
@@ -450,6 +452,70 @@ def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args):
         lat[name + "_p99"] = pct(t, 99)
     lat["single_horizon"] = {"sqp": 50, "kkt": N0}
     return {"latency": lat, "comparators": comp}
+
+
+def measure_lq_workloads(torch, pdilqr, dev, stream, args):
+    """LQ KKT solves alone: the whole-body-sized batch (n = 36, m = 24,
+    N = 100, 1024 instances; 128 distinct instances replicated eight times)
+    with the FP64-residual refinement step, scan vs sequential Riccati, the
+    backward error of every result and the error against the oracle on a
+    sample; and the single-LQR workload (n = 4, m = 2, N = 16) latency."""
+    import oracle   # the error against the FP64 oracle is part of the report
+    out = {}
+    cfg = dict(synth.LQ_WB)
+    uniq, rep = 128, 8
+    insts, _, _, _, _ = synth.ltv_batch(uniq, seed=SEED, **cfg)
+    allinst = [insts[i % uniq] for i in range(uniq * rep)]
+    packed, Nv, off = synth.pack(allinst, synth.LQ_KEYS)
+    s = np.stack([inst["s"] for inst in allinst])
+    lq = {k: torch.tensor(np.asarray(v, np.float32), device=dev) for k, v in packed.items()}
+    lq["S"] = None
+    sd = torch.tensor(np.asarray(s, np.float32), device=dev)
+    wb = {"instances": len(allinst), "distinct": uniq, "n": 36, "m": 24, "N": 100}
+    for name, warps, fn_name in (("scan", 0, "kkt_scan_solve"), ("riccati", 1, "riccati_solve")):
+        plan = pdilqr.Plan(36, 24, Nv, off, warps=warps, refine=True)
+        o = plan.alloc_out(device=dev, want_resid=True)
+        fn = getattr(plan, fn_name)
+        fn(lq, sd, out=o)
+        torch.cuda.synchronize()
+        t = event_times(torch, lambda: fn(lq, sd, out=o), 3, stream)
+        bwd = pdilqr.backward_error(o["resid"]).cpu().numpy()
+        errs = []
+        dx = o["dx"].double().cpu().numpy()
+        for i in range(0, len(allinst), len(allinst) // 4):
+            N, o0 = int(Nv[i]), int(off[i])
+            r32 = {k: np.asarray(allinst[i][k], np.float32).astype(np.float64) for k in synth.LQ_KEYS}
+            ref = oracle.riccati_solve(r32, np.asarray(s[i], np.float32).astype(np.float64))
+            errs.append(float(np.abs(dx[o0:o0 + N + 1] - ref["dx"]).max() / np.abs(ref["dx"]).max()))
+        wb[name] = {"kkt_solves_per_s": len(allinst) / (np.mean(t) / 1e3), "ms": float(np.mean(t)),
+                    "warps": plan.warps, "max_backward_error": float(bwd.max()),
+                    "max_rel_error_vs_oracle_sample": max(errs)}
+        plan.close()
+    out["whole_body_lq_batch"] = wb
+    # single LQR (n = 4, m = 2, N = 16), graph replays
+    inst = synth.ltv_lq(4, 2, 16, seed=0, **{k: v for k, v in synth.LQ_SMALL.items()
+                                             if k not in ("n", "m", "N")})
+    pk, Nv1, off1 = synth.pack([inst], synth.LQ_KEYS)
+    lq1 = {k: torch.tensor(np.asarray(v, np.float32), device=dev) for k, v in pk.items()}
+    lq1["S"] = None
+    s1 = torch.tensor(np.asarray(inst["s"][None], np.float32), device=dev)
+    single = {}
+    for name, fn_name, refine in (("scan", "kkt_scan_solve", False), ("scan_refined", "kkt_scan_solve", True),
+                                  ("riccati", "riccati_solve", False)):
+        p1 = pdilqr.Plan(4, 2, Nv1, off1, refine=refine)
+        o1 = p1.alloc_out(device=dev)
+        fn = getattr(p1, fn_name)
+        fn(lq1, s1, out=o1)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn(lq1, s1, out=o1)
+        for _ in range(10):
+            g.replay()
+        t = event_times(torch, g.replay, args.latency_reps, stream)
+        single[name] = {"p50_us": pct(t, 50) * 1e3, "p99_us": pct(t, 99) * 1e3}
+    out["single_lqr_n4_N16"] = single
+    return out
 
 
 def measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args):
@@ -602,6 +668,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="duration of each serving scenario (0 skips them)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (1/s)")
+    ap.add_argument("--no-lq-workloads", dest="lq_workloads", action="store_false",
+                    help="skip the whole-body LQ batch and single-LQR measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -40,9 +40,20 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // memory with the group's threads.  16-byte copies when every address of the
 // tile is 16-byte aligned by construction (COUNT a multiple of 4 and a 16-byte
 // aligned shared destination and global base), 4-byte copies otherwise.
+// A destination outside shared memory (kernels whose work areas live in a
+// global workspace) is filled with plain vector loads and stores instead.
 template <int COUNT, int NT, bool VEC>
 __device__ __forceinline__ void stage_copy(int t, float* dst, const float* src)
 {
+    if (!__isShared(dst)) {
+        if constexpr (VEC && COUNT % 4 == 0) {
+            for (int e = t; e < COUNT / 4; e += NT)
+                reinterpret_cast<float4*>(dst)[e] = __ldg(reinterpret_cast<const float4*>(src) + e);
+        } else {
+            for (int e = t; e < COUNT; e += NT) dst[e] = src[e];
+        }
+        return;
+    }
     if constexpr (VEC && COUNT % 4 == 0) {
         for (int e = t; e < COUNT / 4; e += NT) cp_async16(dst + 4 * e, src + 4 * e);
     } else {

@@ -47,6 +47,8 @@ struct KktArgs {
     const int32_t* order;                        // [count] CTA -> instance (longest first)
     int32_t* status;                             // [count]
     int count;
+    float* gws;                                  // per-CTA work areas in global memory
+                                                 // (sizes whose areas exceed shared memory)
 };
 
 // ------------------------------------------------------------------ layouts
@@ -610,8 +612,9 @@ __global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) kkt_scan_kernel(c
     const int inst = a.order ? a.order[blockIdx.x] : blockIdx.x;
     if (inst >= a.count) return;
     const LqSource src(a);
+    float* work = a.gws ? a.gws + (int64_t)blockIdx.x * ScanSmem<NX, NU, W>::TOTAL : smem;
     const int st = scan_solve<NX, NU, W>(src, a, a.N[inst], a.off[inst],
-                                         a.s + (int64_t)inst * NX, smem);
+                                         a.s + (int64_t)inst * NX, work);
     if (threadIdx.x == 0) a.status[inst] = st;
 }
 

@@ -24,6 +24,9 @@ struct SizeOps {
     size_t (*sqp_smem)(int warps);
     cudaError_t (*scan_checked)(const KktArgs&, int warps, int64_t limit, cudaStream_t);
     int lq_stage_floats;   // floats of one linearised stage kept by the fused SQP
+    // floats of global workspace per CTA when the scan's work areas do not fit
+    // in shared memory (0: they fit)
+    size_t (*scan_gws_floats)(int warps);
 };
 
 // Tables of the instantiated sizes (one translation unit each).

@@ -13,7 +13,10 @@ static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
 {
     using SM = ScanSmem<NX, NU, W>;
     if constexpr (SM::BYTES > kSmemMax) {
-        return cudaErrorInvalidConfiguration;
+        // work areas in the plan's global workspace
+        if (!a.gws) return cudaErrorInvalidConfiguration;
+        kkt_scan_kernel<NX, NU, W><<<a.count, W * 32, 0, st>>>(a);
+        return cudaGetLastError();
     } else {
     static bool attr_set = false;
     if (!attr_set) {
@@ -56,6 +59,19 @@ static cudaError_t launch_scan_checked(const KktArgs& a, int warps, int64_t limi
         case 8: return launch_scan_checked_w<NX, NU, 8>(a, limit, st);
         case 16: return launch_scan_checked_w<NX, NU, 16>(a, limit, st);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NX, int NU>
+static size_t scan_gws_floats(int warps)
+{
+    auto f = [](size_t total, size_t bytes) { return bytes > kSmemMax ? total : size_t(0); };
+    switch (warps) {
+        case 1: return f(ScanSmem<NX, NU, 1>::TOTAL, ScanSmem<NX, NU, 1>::BYTES);
+        case 4: return f(ScanSmem<NX, NU, 4>::TOTAL, ScanSmem<NX, NU, 4>::BYTES);
+        case 8: return f(ScanSmem<NX, NU, 8>::TOTAL, ScanSmem<NX, NU, 8>::BYTES);
+        case 16: return f(ScanSmem<NX, NU, 16>::TOTAL, ScanSmem<NX, NU, 16>::BYTES);
+        default: return 0;
     }
 }
 
@@ -193,6 +209,7 @@ static SizeOps make_ops()
     o.scan_smem = scan_smem<NX, NU>;
     o.scan_checked = launch_scan_checked<NX, NU>;
     o.lq_stage_floats = StageL<NX, NU>::IN;
+    o.scan_gws_floats = scan_gws_floats<NX, NU>;
     if constexpr (SRBD) {
         o.linearize = launch_linearize<NX, NU>;
         o.merit = launch_merit<NX, NU>;

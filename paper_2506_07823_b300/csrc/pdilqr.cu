@@ -56,6 +56,7 @@ static int pick_warps(const SizeOps* ops, int maxN)
 {
     int w = maxN >= 40 ? 16 : (maxN >= 12 ? 8 : 4);
     while (w > 4 && ops->scan_smem(w) > kSmemMax) w >>= 1;
+    if (ops->scan_smem(w) > kSmemMax) w = maxN >= 40 ? 8 : 4;   // global work areas
     return w;
 }
 
@@ -114,6 +115,7 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
     PD_CUDA(pl->alloc(&pl->ddu, T * m));
     PD_CUDA(pl->alloc(&pl->ddl, T * n));
     if (pl->ops->sqp) PD_CUDA(pl->alloc(&pl->lqcache, T * (size_t)pl->ops->lq_stage_floats));
+    if (const size_t gw = pl->ops->scan_gws_floats(pl->warps)) PD_CUDA(pl->alloc(&pl->gws, C * gw));
     PD_CUDA(cudaMemcpy(pl->dN, hN.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(pl->doff, hoff.data(), C * sizeof(int64_t), cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(pl->dorder, order.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -169,6 +171,7 @@ static KktArgs make_args(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s, f
     a.order = pl->dorder;
     a.status = status;
     a.count = pl->count;
+    a.gws = pl->gws;
     return a;
 }
 
@@ -211,7 +214,7 @@ static pdilqr_status solve_common(pdilqr_plan* pl, const pdilqr_lq* lq, const fl
 {
     if (!pl || !lq_ok(lq) || !s || !out || !out->dx || !out->du || !out->dlam || !out->status)
         return PDILQR_E_INVALID_ARG;
-    if (scan && pl->ops->scan_smem(pl->warps) > kSmemMax) return PDILQR_E_INVALID_ARG;
+    if (scan && pl->ops->scan_smem(pl->warps) > kSmemMax && !pl->gws) return PDILQR_E_INVALID_ARG;
     auto run = [&](const KktArgs& a) -> cudaError_t {
         return scan ? pl->ops->scan(a, pl->warps, st) : pl->ops->riccati(a, st);
     };
@@ -422,6 +425,7 @@ extern "C" pdilqr_status pdilqr_kkt_scan_solve_noalloc(
     a.order = nullptr;
     a.status = status;
     a.count = count;
+    a.gws = nullptr;
     PD_CUDA(ops->scan_checked(a, warps, total_stages, (cudaStream_t)stream));
     return PDILQR_OK;
 }

@@ -24,6 +24,7 @@ struct pdilqr_plan {
     double* norms = nullptr;
     int32_t* st2 = nullptr;
     float* lqcache = nullptr;   // linearised stages kept by the fused SQP (SRBD sizes)
+    float* gws = nullptr;       // per-CTA scan work areas (sizes beyond shared memory)
     int max_count = 0;   // capacity of the batch tables (capacity plans)
 
     template <typename T>

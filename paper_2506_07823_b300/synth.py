@@ -63,8 +63,7 @@ def ltv_lq(n: int, m: int, N: int, seed: int, rho: float = 0.95,
     r = np.zeros((N + 1, m))
     eye = np.eye(n)
     for k in range(N):
-        Ak = eye + 0.1 * g.normal(0.0, 1.0, (n, n))
-        A[k] = rho * Ak / np.max(np.abs(np.linalg.eigvals(Ak)))
+        A[k] = eye + 0.1 * g.normal(0.0, 1.0, (n, n))
         B[k] = g.normal(0.0, b_std, (n, m))
         if q_kind == "diag":
             Q[k] = np.diag(g.uniform(0.1, 1.0, n))
@@ -78,6 +77,9 @@ def ltv_lq(n: int, m: int, N: int, seed: int, rho: float = 0.95,
     Q[N] = terminal_w * eye
     q[N] = g.normal(0.0, 1.0, n)
     s = g.normal(0.0, 1.0, n)
+    # rescale every A_k to spectral radius rho (one batched eigenvalue call)
+    if N > 0:
+        A[:N] *= (rho / np.abs(np.linalg.eigvals(A[:N])).max(axis=1))[:, None, None]
     return {"A": A, "B": B, "c": c, "Q": Q, "R": R, "S": S, "q": q, "r": r, "s": s}
 
 

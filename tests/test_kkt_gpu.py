@@ -90,7 +90,7 @@ def check_parity(insts, Nv, off, out, s, with_S, policy=False):
 
 @pytest.mark.parametrize("solver", ["scan", "riccati"])
 @pytest.mark.parametrize("warps", [4, 8, 16])
-@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (3, 2), (4, 2), (12, 12), (24, 24)])
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (3, 2), (4, 2), (12, 12), (24, 24), (36, 24)])
 def test_ltv_parity_ragged(solver, warps, n, m):
     """Uneven horizons in one batch: N = 1 (degenerate), tiny, and spanning
     several chunks with a ragged tail."""
@@ -157,6 +157,24 @@ def test_refinement_backward_error(solver, n, m):
     assert np.all(b1 <= BWD_TOL), b1
     assert np.all(b1 <= b0 * 1.01 + 1e-12), (b0, b1)
     check_parity(insts, Nv, off, o1, s, False)
+
+
+@pytest.mark.parametrize("solver", ["scan", "riccati"])
+def test_whole_body_sized_workload(solver):
+    """The whole-body-sized LTV batch recipe (n = 36, m = 24, N = 100,
+    spectral radius 0.98, Q = L L^T + 0.1 I, R = 0.01 I) on a few instances,
+    with the FP64-residual refinement step."""
+    cfg = synth.LQ_WB
+    insts, packed, Nv, off, s = make_batch(36, 24, [100, 100, 37], seed=4000, rho=cfg["rho"],
+                                           b_std=cfg["b_std"], q_kind=cfg["q_kind"], r_w=cfg["r_w"])
+    from paper_2506_07823_b300.pdilqr import Plan, backward_error
+    plan = Plan(36, 24, Nv, off, refine=True)
+    lq, sd = to_dev(packed, s, False)
+    fn = plan.kkt_scan_solve if solver == "scan" else plan.riccati_solve
+    out = fn(lq, sd, want_resid=True)
+    torch.cuda.synchronize()
+    check_parity(insts, Nv, off, out, s, False)
+    assert float(backward_error(out["resid"]).max()) <= BWD_TOL
 
 
 def test_residual_kernel_matches_oracle():
