@@ -61,6 +61,22 @@ __device__ __forceinline__ void stage_copy(int t, float* dst, const float* src)
     }
 }
 
+// MUFU reciprocal and reciprocal square root (about 1 ulp); used on the
+// sequential critical path of the factorisations, whose results are FP32 and
+// are corrected by the refinement step where the residual matters.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int NT>
 struct Grp {
     int t;    // rank inside the group
@@ -315,10 +331,10 @@ __device__ bool chol_warp(int lane, float* L, int ld, float* dinv, float* colbuf
     for (int j = 0; j < M; ++j) {
         if (lane == j) {
             const float d = row[j];
-            const float s = sqrtf(fmaxf(d, 1e-30f));
+            const float inv = rsqrt_approx(fmaxf(d, 1e-30f));
             colbuf[M] = (d > 0.f && isfinite(d)) ? 1.f : 0.f;
-            colbuf[M + 1] = s;
-            colbuf[M + 2] = 1.f / s;
+            colbuf[M + 1] = d * inv;
+            colbuf[M + 2] = inv;
         }
         __syncwarp();
         ok = ok && (colbuf[M] != 0.f);
@@ -413,13 +429,21 @@ __device__ bool gj_warp(int lane, float* G, int ld, float* colbuf)
     for (int k = 0; k < N; ++k) {
         float* cb = colbuf + (k & 1) * (N + 1);
         if (lane == k) {
-            int piv = k;
-            float best = fabsf(c[0][k]);
+            // tree argmax of |c[0][i]| over rows k..N-1
+            constexpr int R = N;   // slots; rows below k are masked out
+            float v[R];
+            int id[R];
 #pragma unroll
-            for (int i = k + 1; i < N; ++i) {
-                const float v = fabsf(c[0][i]);
-                if (v > best) { best = v; piv = i; }
+            for (int i = 0; i < R; ++i) {
+                v[i] = (i >= k) ? fabsf(c[0][i]) : -1.f;
+                id[i] = i;
             }
+#pragma unroll
+            for (int w = 1; w < R; w <<= 1)
+#pragma unroll
+                for (int i = 0; i + w < R; i += 2 * w)
+                    if (v[i + w] > v[i]) { v[i] = v[i + w]; id[i] = id[i + w]; }
+            const int piv = id[0];
             float vp = c[0][k];
 #pragma unroll
             for (int i = k + 1; i < N; ++i) vp = (piv == i) ? c[0][i] : vp;
@@ -434,7 +458,7 @@ __device__ bool gj_warp(int lane, float* G, int ld, float* colbuf)
         const int piv = __float_as_int(cb[N]);
         const float pk = cb[k];
         ok = ok && (fabsf(pk) > 1e-30f) && isfinite(pk);
-        const float inv = 1.f / pk;
+        const float inv = rcp_approx(pk);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int j = lane + 32 * q;
