@@ -329,29 +329,31 @@ __device__ bool chol_warp(int lane, float* L, int ld, float* dinv, float* colbuf
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
+        // two alternating slots: a slot is rewritten two columns later, after
+        // every lane has passed the next column's first barrier
+        float* cb = colbuf + (j & 1) * (M + 3);
         if (lane == j) {
             const float d = row[j];
             const float inv = rsqrt_approx(fmaxf(d, 1e-30f));
-            colbuf[M] = (d > 0.f && isfinite(d)) ? 1.f : 0.f;
-            colbuf[M + 1] = d * inv;
-            colbuf[M + 2] = inv;
+            cb[M] = (d > 0.f && isfinite(d)) ? 1.f : 0.f;
+            cb[M + 1] = d * inv;
+            cb[M + 2] = inv;
+            dinv[j] = inv;
         }
         __syncwarp();
-        ok = ok && (colbuf[M] != 0.f);
-        const float inv = colbuf[M + 2];
-        if (lane == j) row[j] = colbuf[M + 1];
+        ok = ok && (cb[M] != 0.f);
+        const float inv = cb[M + 2];
+        if (lane == j) row[j] = cb[M + 1];
         if (lane > j && lane < M) {
             row[j] *= inv;
-            colbuf[lane] = row[j];
+            cb[lane] = row[j];
         }
         __syncwarp();
         if (lane > j && lane < M) {
             const float lij = row[j];
 #pragma unroll
-            for (int k = j + 1; k < M; ++k) row[k] -= lij * colbuf[k];
+            for (int k = j + 1; k < M; ++k) row[k] -= lij * cb[k];
         }
-        if (lane == j) dinv[j] = inv;
-        __syncwarp();
     }
     if (lane < M) {
 #pragma unroll
@@ -463,9 +465,17 @@ __device__ bool gj_warp(int lane, float* G, int ld, float* colbuf)
         for (int q = 0; q < NQ; ++q) {
             const int j = lane + 32 * q;
             if (j <= k || j >= W) continue;
-            float vp = c[q][k];
+            // entry piv of the column by a binary tree of selects
+            float t[N];
 #pragma unroll
-            for (int i = k + 1; i < N; ++i) vp = (piv == i) ? c[q][i] : vp;
+            for (int i = 0; i < N; ++i) t[i] = c[q][i];
+#pragma unroll
+            for (int w = 1; w < N; w <<= 1) {
+                const bool hi = (piv & w) != 0;
+#pragma unroll
+                for (int i = 0; i + w < N; i += 2 * w) t[i] = hi ? t[i + w] : t[i];
+            }
+            const float vp = t[0];
 #pragma unroll
             for (int i = k + 1; i < N; ++i) c[q][i] = (piv == i) ? c[q][k] : c[q][i];
             const float r = vp * inv;

@@ -183,13 +183,14 @@ __device__ void srbd_linearize_stage(const Grp<NT>& g, float* st, const pdilqr_s
             Arow[o + 9 + (r - 3)] = dt;
         } else if (r < 9) {
             const int a = r - 6;
+            const float dtm = dt * rcp_approx(md.mass);
             for (int j = 0; j < 4; ++j)
-                if (sb[j]) Brow[o + 3 * j + a] = dt / md.mass;
+                if (sb[j]) Brow[o + 3 * j + a] = dtm;
         } else {
             const int a = r - 9;
             const float* p = xb;
             const float* w = xb + 9;
-            const float sc = dt / md.inertia[a];
+            const float sc = dt * rcp_approx(md.inertia[a]);
             const float Iw[3] = {md.inertia[0] * w[0], md.inertia[1] * w[1], md.inertia[2] * w[2]};
             for (int l = 0; l < 3; ++l) {
                 // d omega'/d p = I^-1 sum_j s_j [f_j]x
@@ -221,8 +222,17 @@ __device__ void srbd_linearize_stage(const Grp<NT>& g, float* st, const pdilqr_s
                 for (int c = 0; c < 5; ++c) {
                     const float xi = cone_g(c, 0, md.mu_fric) * f[0] + cone_g(c, 1, md.mu_fric) * f[1] +
                                      cone_g(c, 2, md.mu_fric) * f[2];
-                    float v, d1, d2;
-                    barrier3(xi, md.bar_mu, md.bar_delta, v, d1, d2);
+                    // barrier slope and curvature (the value is not needed here)
+                    float d1, d2;
+                    if (xi >= md.bar_delta) {
+                        const float ixi = rcp_approx(xi);
+                        d1 = -md.bar_mu * ixi;
+                        d2 = md.bar_mu * ixi * ixi;
+                    } else {
+                        const float idl = rcp_approx(md.bar_delta);
+                        d1 = md.bar_mu * (xi - 2.f * md.bar_delta) * idl * idl;
+                        d2 = md.bar_mu * idl * idl;
+                    }
                     const float gc = cone_g(c, comp, md.mu_fric);
                     grad += d1 * gc;
                     for (int l = 0; l < 3; ++l)
