@@ -127,6 +127,7 @@ struct LqSource {
         load_stage<NX, NU, NT>(g, st, t, gs, terminal);
     }
     // the caller's arrays are read again in the Riccati sweep: nothing to keep
+    static constexpr bool kKeeps = false;
     template <int NX, int NU, int NT>
     __device__ __forceinline__ void keep(const Grp<NT>&, const float*, int64_t) const {}
     template <int NX, int NU, int NT>
@@ -486,6 +487,14 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
             }
         }
         if (acc != slots + warp * SM::ELEM) copy<E::SIZE, 1, false, 32>(g, slots + warp * SM::ELEM, 1, acc, 1);
+    } else if (Src::kKeeps && active && !last && warp == 0) {
+        // the first chunk has no fold to do: prepare its stages for the sweep
+        // (for sources that linearise on the fly this moves the work off the
+        // sweep's critical path)
+        for (int k = k0; k < k1; ++k) {
+            src.template load<NX, NU, 32>(g, stg, off + k, false);
+            src.template keep<NX, NU, 32>(g, stg, off + k);
+        }
     } else if (active && last) {
         // value-function recursion of the last chunk from the terminal cost
         float* v0 = priv + SM::STG;
@@ -552,8 +561,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         g.sync();
         for (int k = k1 - 1; k >= k0; --k) {
             const int64_t gs = off + k;
-            if (warp > 0) src.template reload<NX, NU, 32>(g, stg, gs);   // kept in phase 1
-            else src.template load<NX, NU, 32>(g, stg, gs, false);
+            src.template reload<NX, NU, 32>(g, stg, gs);   // kept in phase 1
             if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, gs, has_S)) bad = ST_NOT_SPD;
             float* t = v0; v0 = v1; v1 = t;
             __threadfence_block();

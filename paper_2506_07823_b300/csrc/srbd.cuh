@@ -260,6 +260,7 @@ struct SrbdSource {
     const uint8_t* contact;
     int nrob;
     float* cache;                  // per-slot copy of linearised stages (or null)
+    static constexpr bool kKeeps = true;
 
     // Keep a linearised stage (the LQ blocks, StageL::IN floats) so that the
     // Riccati sweep can stream it back instead of linearising again.
