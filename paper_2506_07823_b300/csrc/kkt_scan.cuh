@@ -441,14 +441,19 @@ struct ScanSmem {
 // The scan solve of one instance by the CTA (all threads must call it).
 // src provides the LQ stages; s_inst points to this instance's dx_0 (global
 // or shared memory).  Returns the instance status (uniform over the CTA).
-template <int NX, int NU, int W, class Src>
+//
+// The horizon is split into W chunks, each owned by a unit of UW warps
+// (NT = 32 UW threads: one warp for small states, several for large ones,
+// synchronised by a named barrier per unit).
+template <int NX, int NU, int W, int UW, class Src>
 __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
                           const float* s_inst, float* smem)
 {
     using SM = ScanSmem<NX, NU, W>;
     using E = ElemL<NX>;
-    const int warp = threadIdx.x >> 5;
-    const Grp<32> g{(int)(threadIdx.x & 31), 0};
+    constexpr int NT = 32 * UW;
+    const int warp = threadIdx.x / NT;     // the unit (chunk) of this thread
+    const Grp<NT> g{(int)(threadIdx.x % NT), 1 + warp};
     const int S = N + 1;
     const int Weff = W < S ? W : S;
     const bool has_S = src.has_S();
@@ -476,24 +481,24 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         float* acc = slots + warp * SM::ELEM;
         float* other = tmpE;
         for (int k = k0; k < k1; ++k) {
-            src.template load<NX, NU, 32>(g, stg, off + k, false);
-            src.template keep<NX, NU, 32>(g, stg, off + k);
+            src.template load<NX, NU, NT>(g, stg, off + k, false);
+            src.template keep<NX, NU, NT>(g, stg, off + k);
             if (k == k0) {
-                if (!build_element<NX, NU, 32>(g, stg, acc, scr, has_S, false)) bad = ST_NOT_SPD;
+                if (!build_element<NX, NU, NT>(g, stg, acc, scr, has_S, false)) bad = ST_NOT_SPD;
             } else {
-                if (!build_element<NX, NU, 32>(g, stg, elem, scr, has_S, false)) bad = ST_NOT_SPD;
-                if (!combine_full<NX, 32>(g, acc, elem, other, scr)) bad = ST_SINGULAR;
+                if (!build_element<NX, NU, NT>(g, stg, elem, scr, has_S, false)) bad = ST_NOT_SPD;
+                if (!combine_full<NX, NT>(g, acc, elem, other, scr)) bad = ST_SINGULAR;
                 float* t = acc; acc = other; other = t;
             }
         }
-        if (acc != slots + warp * SM::ELEM) copy<E::SIZE, 1, false, 32>(g, slots + warp * SM::ELEM, 1, acc, 1);
+        if (acc != slots + warp * SM::ELEM) copy<E::SIZE, 1, false, NT>(g, slots + warp * SM::ELEM, 1, acc, 1);
     } else if (Src::kKeeps && active && !last && warp == 0) {
         // the first chunk has no fold to do: prepare its stages for the sweep
         // (for sources that linearise on the fly this moves the work off the
         // sweep's critical path)
         for (int k = k0; k < k1; ++k) {
-            src.template load<NX, NU, 32>(g, stg, off + k, false);
-            src.template keep<NX, NU, 32>(g, stg, off + k);
+            src.template load<NX, NU, NT>(g, stg, off + k, false);
+            src.template keep<NX, NU, NT>(g, stg, off + k);
         }
     } else if (active && last) {
         // value-function recursion of the last chunk from the terminal cost
@@ -501,15 +506,15 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         float* v1 = v0 + SM::ELEM;
         float* scr = v1 + SM::ELEM;
         for (int k = k1 - 1; k >= k0; --k) {
-            src.template load<NX, NU, 32>(g, stg, off + k, k == N);
+            src.template load<NX, NU, NT>(g, stg, off + k, k == N);
             if (k == N) {
-                terminal_value<NX, NU, 32>(g, stg, v0, a, off + k);
+                terminal_value<NX, NU, NT>(g, stg, v0, a, off + k);
             } else {
-                if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, off + k, has_S)) bad = ST_NOT_SPD;
+                if (!riccati_step<NX, NU, NT>(g, stg, v0, v1, scr, a, off + k, has_S)) bad = ST_NOT_SPD;
                 float* t = v0; v0 = v1; v1 = t;
             }
         }
-        copy<E::SIZE, 1, false, 32>(g, slots + warp * SM::ELEM, 1, v0, 1);
+        copy<E::SIZE, 1, false, NT>(g, slots + warp * SM::ELEM, 1, v0, 1);
     }
     __syncthreads();
 
@@ -528,17 +533,17 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
                 vf = (j + 2 * d - 1 >= J - 1);
                 const float* e1 = slots + (j + 1) * SM::ELEM;
                 const float* e2 = slots + (j + 1 + d) * SM::ELEM;
-                const bool ok = vf ? combine_vf<NX, 32>(g, e1, e2, res, scr)
-                                   : combine_full<NX, 32>(g, e1, e2, res, scr + SM::ELEM);
+                const bool ok = vf ? combine_vf<NX, NT>(g, e1, e2, res, scr)
+                                   : combine_full<NX, NT>(g, e1, e2, res, scr + SM::ELEM);
                 if (!ok) bad = ST_SINGULAR;
             }
             __syncthreads();
             if (act) {
                 float* dst = slots + (j + 1) * SM::ELEM;
                 if (vf) {
-                    copy<NX * NX + NX, 1, false, 32>(g, dst + E::P, 1, res + E::P, 1);
+                    copy<NX * NX + NX, 1, false, NT>(g, dst + E::P, 1, res + E::P, 1);
                 } else {
-                    copy<E::SIZE, 1, false, 32>(g, dst, 1, res, 1);
+                    copy<E::SIZE, 1, false, NT>(g, dst, 1, res, 1);
                 }
             }
             __syncthreads();
@@ -555,27 +560,27 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         float* v0 = priv + SM::STG;
         float* v1 = v0 + SM::ELEM;
         float* scr = v1 + SM::ELEM;
-        copy<NX * NX + NX, 1, false, 32, false>(g, v0 + E::P, 1, slots + (warp + 1) * SM::ELEM + E::P, 1);
-        fill<NX, NX, 32, false>(g, psiA, NX, 0.f, 1.f);
-        for (int i = g.t; i < NX; i += 32) psiv[i] = 0.f;
+        copy<NX * NX + NX, 1, false, NT, false>(g, v0 + E::P, 1, slots + (warp + 1) * SM::ELEM + E::P, 1);
+        fill<NX, NX, NT, false>(g, psiA, NX, 0.f, 1.f);
+        for (int i = g.t; i < NX; i += NT) psiv[i] = 0.f;
         g.sync();
         for (int k = k1 - 1; k >= k0; --k) {
             const int64_t gs = off + k;
-            src.template reload<NX, NU, 32>(g, stg, gs);   // kept in phase 1
-            if (!riccati_step<NX, NU, 32>(g, stg, v0, v1, scr, a, gs, has_S)) bad = ST_NOT_SPD;
+            src.template reload<NX, NU, NT>(g, stg, gs);   // kept in phase 1
+            if (!riccati_step<NX, NU, NT>(g, stg, v0, v1, scr, a, gs, has_S)) bad = ST_NOT_SPD;
             float* t = v0; v0 = v1; v1 = t;
             __threadfence_block();
             g.sync();
             // psi <- Psi bbar_k + psi ;  Psi <- Psi Abar_k
-            mm<NX, 1, NX, false, false, 32, false>(g, psitmp, 1, psiA, NX, a.bbar + gs * NX, 1, psiv, 1);
-            mm<NX, NX, NX, false, false, 32, false>(g, psiB, NX, psiA, NX, a.Abar + gs * NX * NX, NX);
+            mm<NX, 1, NX, false, false, NT, false>(g, psitmp, 1, psiA, NX, a.bbar + gs * NX, 1, psiv, 1);
+            mm<NX, NX, NX, false, false, NT, false>(g, psiB, NX, psiA, NX, a.Abar + gs * NX * NX, NX);
             g.sync();
-            for (int i = g.t; i < NX; i += 32) psiv[i] = psitmp[i];
+            for (int i = g.t; i < NX; i += NT) psiv[i] = psitmp[i];
             float* t2 = psiA; psiA = psiB; psiB = t2;
             g.sync();
         }
         // publish Psi, psi at fixed slots of this warp's area
-        if (psiA != priv + SM::PSI) copy<NX * NX, 1, false, 32>(g, priv + SM::PSI, 1, psiA, 1);
+        if (psiA != priv + SM::PSI) copy<NX * NX, 1, false, NT>(g, priv + SM::PSI, 1, psiA, 1);
     }
     if (bad != ST_OK && g.t == 0) atomicMax(st_word, bad);
     __syncthreads();
@@ -584,12 +589,12 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     // chunk maps, then every chunk rolls out dx, du, dlam.
     if (warp == 0) {
         float* x = xs;
-        for (int i = g.t; i < NX; i += 32) x[i] = s_inst[i];
+        for (int i = g.t; i < NX; i += NT) x[i] = s_inst[i];
         g.sync();
         for (int w = 0; w + 1 < Weff; ++w) {
             const float* Psi = smem + SM::SLOTS + w * SM::PRIV + SM::PSI;
             const float* psv = Psi + 2 * NX * NX;
-            mv<NX, NX, false, 32>(g, xs + (w + 1) * round4(NX), Psi, NX, xs + w * round4(NX), psv);
+            mv<NX, NX, false, NT>(g, xs + (w + 1) * round4(NX), Psi, NX, xs + w * round4(NX), psv);
         }
     }
     __syncthreads();
@@ -597,9 +602,9 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         float* x = priv;                 // reuse the private area
         float* xn = priv + round4(NX);
         float* rb = priv + 2 * round4(NX);
-        for (int i = g.t; i < NX; i += 32) x[i] = xs[warp * round4(NX) + i];
+        for (int i = g.t; i < NX; i += NT) x[i] = xs[warp * round4(NX) + i];
         g.sync();
-        rollout_chunk<NX, NU, 32>(g, x, xn, rb, a, off, N, k0, k1);
+        rollout_chunk<NX, NU, NT>(g, x, xn, rb, a, off, N, k0, k1);
     }
     __syncthreads();
     const int status = st_word[0];
@@ -607,22 +612,30 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     return status;
 }
 
+// Warps per unit (one horizon chunk): one warp for small states, a group of
+// warps for large ones.
+template <int NX>
+struct UnitWarps {
+    static constexpr int value = NX <= 24 ? 1 : (NX <= 48 ? 4 : 8);
+};
+
 // CTAs per SM the register budget is sized for (128 registers per thread at most)
 template <int W>
 struct MinBlocks {
     static constexpr int value = W >= 16 ? 1 : (W >= 8 ? 2 : (W >= 4 ? 4 : 16));
 };
 
-template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) kkt_scan_kernel(const __grid_constant__ KktArgs a)
+template <int NX, int NU, int W, int UW>
+__global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
+    kkt_scan_kernel(const __grid_constant__ KktArgs a)
 {
     extern __shared__ __align__(16) float smem[];
     const int inst = a.order ? a.order[blockIdx.x] : blockIdx.x;
     if (inst >= a.count) return;
     const LqSource src(a);
     float* work = a.gws ? a.gws + (int64_t)blockIdx.x * ScanSmem<NX, NU, W>::TOTAL : smem;
-    const int st = scan_solve<NX, NU, W>(src, a, a.N[inst], a.off[inst],
-                                         a.s + (int64_t)inst * NX, work);
+    const int st = scan_solve<NX, NU, W, UW>(src, a, a.N[inst], a.off[inst],
+                                             a.s + (int64_t)inst * NX, work);
     if (threadIdx.x == 0) a.status[inst] = st;
 }
 
@@ -645,7 +658,7 @@ __global__ void __launch_bounds__(W * 32, MinBlocks<W>::value)
         return;
     }
     const LqSource src(a);
-    const int st = scan_solve<NX, NU, W>(src, a, N, off, a.s + (int64_t)inst * NX, smem);
+    const int st = scan_solve<NX, NU, W, 1>(src, a, N, off, a.s + (int64_t)inst * NX, smem);
     if (threadIdx.x == 0) a.status[inst] = st;
 }
 

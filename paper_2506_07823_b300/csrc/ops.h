@@ -27,7 +27,18 @@ struct SizeOps {
     // floats of global workspace per CTA when the scan's work areas do not fit
     // in shared memory (0: they fit)
     size_t (*scan_gws_floats)(int warps);
+    int unit_warps;        // warps per horizon chunk; warps x unit_warps <= 32
 };
+
+// Warp counts (horizon chunks) a size supports: 1, 4, 8 or 16 within the
+// 1024-thread block limit.
+inline bool warps_ok(const SizeOps* o, int w)
+{
+    return (w == 1 || w == 4 || w == 8 || w == 16) && w * o->unit_warps <= 32;
+}
+
+// The kernel table of an (n, m) size, or null when it is not instantiated.
+const SizeOps* find_ops(int n, int m);
 
 // Tables of the instantiated sizes (one translation unit each).
 const SizeOps* ops_small(int n, int m);   // (1,1) (2,1) (3,2) (4,2)

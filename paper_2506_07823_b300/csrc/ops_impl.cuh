@@ -8,26 +8,33 @@
 namespace pdl {
 
 
+// W horizon chunks, each owned by UnitWarps<NX> warps; a (W, unit) pair above
+// the 1024-thread block limit is not instantiated.
 template <int NX, int NU, int W>
 static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
 {
+    constexpr int UW = UnitWarps<NX>::value;
     using SM = ScanSmem<NX, NU, W>;
-    if constexpr (SM::BYTES > kSmemMax) {
+    if constexpr (W * UW * 32 > 1024) {
+        return cudaErrorInvalidConfiguration;
+    } else if constexpr (SM::BYTES > kSmemMax) {
         // work areas in the plan's global workspace
         if (!a.gws) return cudaErrorInvalidConfiguration;
-        kkt_scan_kernel<NX, NU, W><<<a.count, W * 32, 0, st>>>(a);
+        kkt_scan_kernel<NX, NU, W, UW><<<a.count, W * 32 * UW, 0, st>>>(a);
         return cudaGetLastError();
     } else {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kkt_scan_kernel<NX, NU, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SM::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    kkt_scan_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a);
-    return cudaGetLastError();
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(kkt_scan_kernel<NX, NU, W, UW>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)SM::BYTES);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        KktArgs b = a;
+        b.gws = nullptr;          // the work areas fit in shared memory
+        kkt_scan_kernel<NX, NU, W, UW><<<a.count, W * 32 * UW, SM::BYTES, st>>>(b);
+        return cudaGetLastError();
     }
 }
 
@@ -62,15 +69,24 @@ static cudaError_t launch_scan_checked(const KktArgs& a, int warps, int64_t limi
     }
 }
 
+// Floats of global workspace per CTA (0 when the work areas fit in shared
+// memory or the warp count is not available for this size).
+template <int NX, int NU, int W>
+static size_t scan_gws_floats_w()
+{
+    using SM = ScanSmem<NX, NU, W>;
+    if (W * UnitWarps<NX>::value * 32 > 1024) return 0;
+    return SM::BYTES > kSmemMax ? SM::TOTAL : 0;
+}
+
 template <int NX, int NU>
 static size_t scan_gws_floats(int warps)
 {
-    auto f = [](size_t total, size_t bytes) { return bytes > kSmemMax ? total : size_t(0); };
     switch (warps) {
-        case 1: return f(ScanSmem<NX, NU, 1>::TOTAL, ScanSmem<NX, NU, 1>::BYTES);
-        case 4: return f(ScanSmem<NX, NU, 4>::TOTAL, ScanSmem<NX, NU, 4>::BYTES);
-        case 8: return f(ScanSmem<NX, NU, 8>::TOTAL, ScanSmem<NX, NU, 8>::BYTES);
-        case 16: return f(ScanSmem<NX, NU, 16>::TOTAL, ScanSmem<NX, NU, 16>::BYTES);
+        case 1: return scan_gws_floats_w<NX, NU, 1>();
+        case 4: return scan_gws_floats_w<NX, NU, 4>();
+        case 8: return scan_gws_floats_w<NX, NU, 8>();
+        case 16: return scan_gws_floats_w<NX, NU, 16>();
         default: return 0;
     }
 }
@@ -156,20 +172,28 @@ static cudaError_t launch_merit(const MeritArgs& a, cudaStream_t st)
 template <int NX, int NU, int W>
 static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
 {
+    constexpr int UW = UnitWarps<NX>::value;
     using SM = SqpSmem<NX, NU, W>;
-    if constexpr (SM::BYTES > kSmemMax) {
+    if constexpr (W * UW * 32 > 1024) {
         return cudaErrorInvalidConfiguration;
     } else {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sqp_kernel<NX, NU, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SM::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    sqp_kernel<NX, NU, W><<<a.ka.count, W * 32, SM::BYTES, st>>>(a);
-    return cudaGetLastError();
+        // scan work areas in shared memory when they fit, else in the plan's
+        // global workspace with the line-search extras alone in shared memory
+        constexpr bool GWS = SM::SC::BYTES > kSmemMax;
+        constexpr size_t bytes = GWS ? SM::EXTRA_BYTES : SM::BYTES;
+        if (GWS && !a.ka.gws) return cudaErrorInvalidConfiguration;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(sqp_kernel<NX, NU, W, UW>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)bytes);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        SqpArgs b = a;
+        if (!GWS) b.ka.gws = nullptr;
+        sqp_kernel<NX, NU, W, UW><<<a.ka.count, W * 32 * UW, bytes, st>>>(b);
+        return cudaGetLastError();
     }
 }
 
@@ -185,15 +209,26 @@ static cudaError_t launch_sqp(const SqpArgs& a, int warps, cudaStream_t st)
     }
 }
 
+// Dynamic shared memory of the fused kernel (its extras alone when the scan
+// work areas live in the global workspace); SIZE_MAX when the warp count is
+// not available for this size.
+template <int NX, int NU, int W>
+static size_t sqp_smem_w()
+{
+    using SM = SqpSmem<NX, NU, W>;
+    if (W * UnitWarps<NX>::value * 32 > 1024) return SIZE_MAX;
+    return SM::SC::BYTES > kSmemMax ? SM::EXTRA_BYTES : SM::BYTES;
+}
+
 template <int NX, int NU>
 static size_t sqp_smem(int warps)
 {
     switch (warps) {
-        case 1: return SqpSmem<NX, NU, 1>::BYTES;
-        case 4: return SqpSmem<NX, NU, 4>::BYTES;
-        case 8: return SqpSmem<NX, NU, 8>::BYTES;
-        case 16: return SqpSmem<NX, NU, 16>::BYTES;
-        default: return 0;
+        case 1: return sqp_smem_w<NX, NU, 1>();
+        case 4: return sqp_smem_w<NX, NU, 4>();
+        case 8: return sqp_smem_w<NX, NU, 8>();
+        case 16: return sqp_smem_w<NX, NU, 16>();
+        default: return SIZE_MAX;
     }
 }
 
@@ -210,6 +245,7 @@ static SizeOps make_ops()
     o.scan_checked = launch_scan_checked<NX, NU>;
     o.lq_stage_floats = StageL<NX, NU>::IN;
     o.scan_gws_floats = scan_gws_floats<NX, NU>;
+    o.unit_warps = UnitWarps<NX>::value;
     if constexpr (SRBD) {
         o.linearize = launch_linearize<NX, NU>;
         o.merit = launch_merit<NX, NU>;

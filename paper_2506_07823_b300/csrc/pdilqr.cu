@@ -42,7 +42,7 @@ static pdilqr_status cuda_status(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_status(e_);         \
     } while (0)
 
-static const SizeOps* find_ops(int n, int m)
+const SizeOps* pdl::find_ops(int n, int m)
 {
     for (auto f : {ops_small, ops_12, ops_24, ops_36})
         if (const SizeOps* o = f(n, m)) return o;
@@ -55,8 +55,11 @@ static const SizeOps* find_ops(int n, int m)
 static int pick_warps(const SizeOps* ops, int maxN)
 {
     int w = maxN >= 40 ? 16 : (maxN >= 12 ? 8 : 4);
-    while (w > 4 && ops->scan_smem(w) > kSmemMax) w >>= 1;
-    if (ops->scan_smem(w) > kSmemMax) w = maxN >= 40 ? 8 : 4;   // global work areas
+    while (w > 4 && (!warps_ok(ops, w) || ops->scan_smem(w) > kSmemMax)) w >>= 1;
+    if (ops->scan_smem(w) > kSmemMax) {
+        w = maxN >= 40 ? 8 : 4;   // global work areas
+        while (w > 1 && !warps_ok(ops, w)) w >>= 1;
+    }
     return w;
 }
 
@@ -83,8 +86,7 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
         if (hoff[pa] + hN[pa] + 1 > hoff[pb]) return PDILQR_E_INVALID_ARG;
     }
     pl->warps = (o && o->warps) ? o->warps : pick_warps(pl->ops, pl->maxN);
-    if (pl->warps != 1 && pl->warps != 4 && pl->warps != 8 && pl->warps != 16)
-        return PDILQR_E_INVALID_ARG;
+    if (!warps_ok(pl->ops, pl->warps)) return PDILQR_E_INVALID_ARG;
     pl->refine = (o && o->refine) ? 1 : 0;
     // longest horizons first: the tail of the grid holds the short instances
     std::vector<int32_t> order(b->count);
@@ -330,6 +332,7 @@ extern "C" pdilqr_status pdilqr_solve(pdilqr_plan* pl, const pdilqr_srbd_model* 
         return PDILQR_E_INVALID_ARG;
     if (o->max_iters < 1 || o->max_iters > 32) return PDILQR_E_INVALID_ARG;
     if (pl->ops->sqp_smem(pl->warps) > kSmemMax) return PDILQR_E_INVALID_ARG;
+    if (pl->ops->scan_gws_floats(pl->warps) && !pl->gws) return PDILQR_E_INVALID_ARG;
     SqpArgs a;
     a.md = *md;
     a.x0hat = x0hat;
@@ -436,7 +439,7 @@ pdilqr_status pdl::plan_create_capacity(int n, int m, int max_count, int64_t slo
 {
     *out = nullptr;
     const SizeOps* ops = find_ops(n, m);
-    if (!ops || max_count < 1 || slots < 2) return PDILQR_E_INVALID_ARG;
+    if (!ops || max_count < 1 || slots < 2 || !warps_ok(ops, warps)) return PDILQR_E_INVALID_ARG;
     pdilqr_plan* pl = new (std::nothrow) pdilqr_plan();
     if (!pl) return PDILQR_E_NO_MEMORY;
     pl->n = n;
@@ -465,6 +468,7 @@ pdilqr_status pdl::plan_create_capacity(int n, int m, int max_count, int64_t slo
     chk(pl->alloc(&pl->ddu, T * m));
     chk(pl->alloc(&pl->ddl, T * n));
     if (ops->sqp) chk(pl->alloc(&pl->lqcache, T * (size_t)ops->lq_stage_floats));
+    if (const size_t gw = ops->scan_gws_floats(warps)) chk(pl->alloc(&pl->gws, C * gw));
     if (e != cudaSuccess) {
         delete pl;
         return cuda_status(e);

@@ -275,13 +275,21 @@ pdilqr_status ensure_res(pdilqr_server* sv, Slot& sl, int cls)
     const size_t B = sv->opts.max_batch, S = B * ((size_t)sv->opts.max_N + 1);
     r.n = n;
     r.nc = nc;
-    pdilqr_status ps = plan_create_capacity(n, n, (int)B, (int64_t)S, sv->opts.warps, &r.plan);
-    if (ps != PDILQR_OK) return ps;
-    // the largest warp count not above the requested one whose fused kernel fits
+    // the largest warp count not above the requested one whose fused kernel
+    // fits in shared memory; sizes that fit with none run the requested count
+    // (clamped to the size's limit) from the global workspace
+    const SizeOps* ops = find_ops(n, n);
+    if (!ops || !ops->sqp) return PDILQR_E_INVALID_ARG;
+    auto smaller = [](int x) { return x == 16 ? 8 : (x == 8 ? 4 : 1); };
     int w = sv->opts.warps;
-    while (w > 1 && (!r.plan->ops->sqp_smem || r.plan->ops->sqp_smem(w) > kSmemMax))
-        w = (w == 16) ? 8 : (w == 8 ? 4 : 1);
-    r.plan->warps = w;
+    while (w > 1 && (!warps_ok(ops, w) || ops->sqp_smem(w) > kSmemMax || ops->scan_gws_floats(w)))
+        w = smaller(w);
+    if (ops->scan_gws_floats(w) || ops->sqp_smem(w) > kSmemMax) {
+        w = sv->opts.warps;
+        while (w > 1 && !warps_ok(ops, w)) w = smaller(w);
+    }
+    pdilqr_status ps = plan_create_capacity(n, n, (int)B, (int64_t)S, w, &r.plan);
+    if (ps != PDILQR_OK) return ps;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
     chk(dalloc(r, &r.px, S * n)); chk(dalloc(r, &r.pu, S * n)); chk(dalloc(r, &r.pl, S * n));

@@ -36,13 +36,19 @@ struct SqpSmem {
     static constexpr int CTL = SBUF + round4(NX);
     static constexpr int TOTAL = CTL + 8;
     static constexpr size_t BYTES = sizeof(float) * TOTAL;
+    static constexpr size_t EXTRA_BYTES = sizeof(float) * (TOTAL - MER);   // extras only
 };
 
-template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) sqp_kernel(const __grid_constant__ SqpArgs a)
+template <int NX, int NU, int W, int UW>
+__global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
+    sqp_kernel(const __grid_constant__ SqpArgs a)
 {
     using SM = SqpSmem<NX, NU, W>;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(16) float smem_all[];
+    // scan work areas in shared memory, or in a per-CTA global slice for
+    // states whose areas do not fit (shared memory then holds the extras only)
+    float* work = a.ka.gws ? a.ka.gws + (int64_t)blockIdx.x * SM::SC::TOTAL : smem_all;
+    float* smem = a.ka.gws ? smem_all - SM::MER : smem_all;
     const int inst = a.ka.order ? a.ka.order[blockIdx.x] : blockIdx.x;
     if (inst >= a.ka.count) return;
     const int N = a.ka.N[inst];
@@ -69,7 +75,7 @@ __global__ void __launch_bounds__(W * 32, MinBlocks<W>::value) sqp_kernel(const 
     for (int it = 0; it < a.max_iters; ++it) {
         for (int i = threadIdx.x; i < NX; i += blockDim.x) sbuf[i] = xh[i] - x[i];
         __syncthreads();
-        const int st = scan_solve<NX, NU, W>(src, a.ka, N, off, sbuf, smem);
+        const int st = scan_solve<NX, NU, W, UW>(src, a.ka, N, off, sbuf, work);
         if (st != ST_OK) {
             status = st;
             break;

@@ -98,6 +98,8 @@ def test_ltv_parity_ragged(solver, warps, n, m):
         pytest.skip("warp count only affects the scan")
     if n == 24 and warps != 4:
         pytest.skip("n = 24 fits shared memory with 4 warps per instance only")
+    if n == 36 and warps == 16:
+        pytest.skip("n = 36 runs chunks of 4 warps: at most 8 chunks per 1024-thread CTA")
     Ns = [1, 2, 3, 5, 16, 17, 50, 100]
     insts, packed, Nv, off, s = make_batch(n, m, Ns, seed=100 * n + m)
     from paper_2506_07823_b300.pdilqr import Plan
