@@ -186,8 +186,7 @@ PDILQR_API int64_t pdilqr_noalloc_capacity_stages(int32_t n, int32_t m);
  * 0.5 w_form sum_a |p_a - p_{a+1 mod nrob} - d_form[a]|^2 is added at every
  * stage.  The Hessian is the Gauss-Newton one of Sec. II-F. */
 typedef struct {
-    int32_t nrob;              /* robots stacked in one state (1 supported by   */
-                               /* the fused solver, up to 16 by linearize)      */
+    int32_t nrob;              /* robots stacked in one state: 1, 2, 4, 8, 16   */
     float w_form;              /* formation weight                              */
     float d_form[16][3];       /* formation offsets                             */
     float mass, inertia[3], dt, gravity;
@@ -258,7 +257,9 @@ typedef struct {
  * x += a dx, u += a du, lam += a dlam (Eq. linear_rollout), all in one
  * kernel with one CTA per instance and no host synchronisation.  x, u, lam
  * (device, trajectory layout) hold the warm start on entry and the solution
- * on exit.  Needs n = m = 12 (nrob = 1). */
+ * on exit.  Needs n = m = 12 nrob with nrob in {1, 2, 4, 8, 16}.  Sizes
+ * whose work areas exceed shared memory (nrob >= 8) run them from a global
+ * workspace the plan allocates. */
 PDILQR_API pdilqr_status pdilqr_solve(pdilqr_plan *plan, const pdilqr_srbd_model *model,
                                       const pdilqr_sqp_opts *opts, const float *x0hat,
                                       float *x, float *u, float *lam, const float *xref,
@@ -284,15 +285,23 @@ typedef struct {
     int32_t max_inflight;      /* batches in flight on separate streams (0: 2)    */
     int32_t max_N;             /* longest horizon a client may use (0: 100)       */
     int32_t sqp_iters;         /* SQP iterations per request (0: 1)               */
-    int32_t warps;             /* warps per instance (0: 8; 1: sequential Riccati)*/
+    int32_t warps;             /* horizon chunks per instance, an upper bound    */
+                               /* (0: 8; 1: sequential Riccati); a size class   */
+                               /* runs the largest count whose fused kernel     */
+                               /* fits shared memory, else 1                     */
     int32_t batch_window_us;   /* how long the dispatcher waits for more requests */
                                /* once it has one and a stream is free (0: none)  */
     pdilqr_srbd_model model;   /* robot and formation constants (shared by all    */
                                /* clients); nrob is taken per client              */
+    const pdilqr_srbd_model *class_models;  /* HOST [5] or NULL: the constants of */
+                               /* the classes nrob = 1, 2, 4, 8, 16 (their nrob    */
+                               /* fields are ignored; read during create only);    */
+                               /* NULL: `model` for every class                    */
 } pdilqr_serve_opts;
 
 typedef struct {
-    int32_t nrob;              /* robots of this client (n = m = 12 nrob); fixed  */
+    int32_t nrob;              /* robots of this client: 1, 2, 4, 8 or 16        */
+                               /* (n = m = 12 nrob); fixed                        */
     int32_t N;                 /* horizon of this client; fixed                   */
     int32_t reset;             /* 1: re-initialise the warm start from x0hat      */
     const float *x0hat;        /* HOST [n] measured state                         */

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kkt_scan.cuh"
 #include "residual.cuh"
 #include "sqp.cuh"
@@ -28,6 +30,7 @@ struct SizeOps {
     // in shared memory (0: they fit)
     size_t (*scan_gws_floats)(int warps);
     int unit_warps;        // warps per horizon chunk; warps x unit_warps <= 32
+    size_t lin_ws_floats;  // global workspace of the standalone linearisation (0: none)
 };
 
 // Warp counts (horizon chunks) a size supports: 1, 4, 8 or 16 within the
@@ -45,5 +48,8 @@ const SizeOps* ops_small(int n, int m);   // (1,1) (2,1) (3,2) (4,2)
 const SizeOps* ops_12(int n, int m);      // (12,12): SRBD, fused SQP
 const SizeOps* ops_24(int n, int m);      // (24,24): two stacked robots
 const SizeOps* ops_36(int n, int m);      // (36,24): Riccati comparator, residual
+const SizeOps* ops_48(int n, int m);      // (48,48): four robots
+const SizeOps* ops_96(int n, int m);      // (96,96): eight robots
+const SizeOps* ops_192(int n, int m);     // (192,192): sixteen robots
 
 }  // namespace pdl

@@ -122,8 +122,10 @@ static cudaError_t launch_riccati(const KktArgs& a, cudaStream_t st)
     // warps (instances) per block: up to 4, as many as fit in shared memory
     constexpr int FIT = (int)((227 * 1024) / SM::BYTES);
     constexpr int WPB = FIT >= 4 ? 4 : (FIT >= 1 ? FIT : 1);
-    const size_t bytes = SM::BYTES * WPB;
-    if (bytes > kSmemMax) return cudaErrorInvalidConfiguration;
+    constexpr size_t bytes = SM::BYTES * WPB;
+    if constexpr (bytes > kSmemMax) {
+        return cudaErrorInvalidConfiguration;
+    } else {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(riccati_kernel<NX, NU>,
@@ -135,6 +137,7 @@ static cudaError_t launch_riccati(const KktArgs& a, cudaStream_t st)
     const int grid = (a.count + WPB - 1) / WPB;
     riccati_kernel<NX, NU><<<grid, 32 * WPB, bytes, st>>>(a);
     return cudaGetLastError();
+    }
 }
 
 template <int NX, int NU>
@@ -145,21 +148,52 @@ static cudaError_t launch_resid(const ResidArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Stage slots per block of the standalone linearisation and where its stage
+// areas live: four one-warp units in shared memory for small states, one
+// unit per block for larger ones, a global workspace beyond shared memory.
+template <int NX, int NU>
+struct LinCfg {
+    static constexpr size_t STAGE_BYTES = sizeof(float) * StageL<NX, NU>::SIZE;
+    static constexpr int UW = UnitWarps<NX>::value;
+    static constexpr int SPB = (UW == 1 && 4 * STAGE_BYTES <= kSmemMax) ? 4 : 1;
+    static constexpr bool GLOBAL = SPB * STAGE_BYTES > kSmemMax;
+    static constexpr int GLOBAL_BLOCKS = 2 * 148;   // blocks of the global-workspace form
+};
+
+template <int NX, int NU>
+static size_t lin_ws_floats()
+{
+    using C = LinCfg<NX, NU>;
+    return C::GLOBAL ? (size_t)C::GLOBAL_BLOCKS * StageL<NX, NU>::SIZE : 0;
+}
+
 template <int NX, int NU>
 static cudaError_t launch_linearize(const LinArgs& a, cudaStream_t st)
 {
-    const size_t bytes = sizeof(float) * StageL<NX, NU>::SIZE * 4;
-    if (bytes > kSmemMax) return cudaErrorInvalidConfiguration;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(linearize_kernel<NX, NU>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    using C = LinCfg<NX, NU>;
+    constexpr int THREADS = C::SPB * 32 * C::UW;
+    if (a.total <= 0) return cudaSuccess;
+    if constexpr (C::GLOBAL) {
+        if (!a.work) return cudaErrorInvalidConfiguration;
+        const int64_t blocks = std::min<int64_t>(a.total, C::GLOBAL_BLOCKS);
+        linearize_kernel<NX, NU, C::SPB, C::UW><<<(unsigned)blocks, THREADS, 0, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        constexpr size_t bytes = C::SPB * C::STAGE_BYTES;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(linearize_kernel<NX, NU, C::SPB, C::UW>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)bytes);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        LinArgs b = a;
+        b.work = nullptr;
+        const int64_t blocks = (a.total + C::SPB - 1) / C::SPB;
+        linearize_kernel<NX, NU, C::SPB, C::UW><<<(unsigned)blocks, THREADS, bytes, st>>>(b);
+        return cudaGetLastError();
     }
-    const int64_t blocks = (a.total + 3) / 4;
-    linearize_kernel<NX, NU><<<(unsigned)blocks, 128, bytes, st>>>(a);
-    return cudaGetLastError();
 }
 
 template <int NX, int NU>
@@ -248,6 +282,7 @@ static SizeOps make_ops()
     o.unit_warps = UnitWarps<NX>::value;
     if constexpr (SRBD) {
         o.linearize = launch_linearize<NX, NU>;
+        o.lin_ws_floats = lin_ws_floats<NX, NU>();
         o.merit = launch_merit<NX, NU>;
     }
     if constexpr (FUSED) {

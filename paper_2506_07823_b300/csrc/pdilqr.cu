@@ -44,7 +44,7 @@ static pdilqr_status cuda_status(cudaError_t e)
 
 const SizeOps* pdl::find_ops(int n, int m)
 {
-    for (auto f : {ops_small, ops_12, ops_24, ops_36})
+    for (auto f : {ops_small, ops_12, ops_24, ops_36, ops_48, ops_96, ops_192})
         if (const SizeOps* o = f(n, m)) return o;
     return nullptr;
 }
@@ -116,8 +116,11 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
     PD_CUDA(pl->alloc(&pl->ddx, T * n));
     PD_CUDA(pl->alloc(&pl->ddu, T * m));
     PD_CUDA(pl->alloc(&pl->ddl, T * n));
-    if (pl->ops->sqp) PD_CUDA(pl->alloc(&pl->lqcache, T * (size_t)pl->ops->lq_stage_floats));
+    // linearised-stage cache of the fused SQP (the one-chunk sweep linearises once)
+    if (pl->ops->sqp && pl->warps > 1)
+        PD_CUDA(pl->alloc(&pl->lqcache, T * (size_t)pl->ops->lq_stage_floats));
     if (const size_t gw = pl->ops->scan_gws_floats(pl->warps)) PD_CUDA(pl->alloc(&pl->gws, C * gw));
+    if (pl->ops->lin_ws_floats) PD_CUDA(pl->alloc(&pl->lin_ws, pl->ops->lin_ws_floats));
     PD_CUDA(cudaMemcpy(pl->dN, hN.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(pl->doff, hoff.data(), C * sizeof(int64_t), cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(pl->dorder, order.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -297,6 +300,7 @@ extern "C" pdilqr_status pdilqr_linearize(pdilqr_plan* pl, const pdilqr_srbd_mod
     a.off = pl->doff;
     a.stage_inst = pl->dstage_inst;
     a.total = pl->total;
+    a.work = pl->lin_ws;
     PD_CUDA(pl->ops->linearize(a, (cudaStream_t)stream));
     return PDILQR_OK;
 }
@@ -467,7 +471,7 @@ pdilqr_status pdl::plan_create_capacity(int n, int m, int max_count, int64_t slo
     chk(pl->alloc(&pl->ddx, T * n));
     chk(pl->alloc(&pl->ddu, T * m));
     chk(pl->alloc(&pl->ddl, T * n));
-    if (ops->sqp) chk(pl->alloc(&pl->lqcache, T * (size_t)ops->lq_stage_floats));
+    if (ops->sqp && warps > 1) chk(pl->alloc(&pl->lqcache, T * (size_t)ops->lq_stage_floats));
     if (const size_t gw = ops->scan_gws_floats(warps)) chk(pl->alloc(&pl->gws, C * gw));
     if (e != cudaSuccess) {
         delete pl;

@@ -25,6 +25,7 @@ struct pdilqr_plan {
     int32_t* st2 = nullptr;
     float* lqcache = nullptr;   // linearised stages kept by the fused SQP (SRBD sizes)
     float* gws = nullptr;       // per-CTA scan work areas (sizes beyond shared memory)
+    float* lin_ws = nullptr;    // stage areas of the standalone linearisation (large sizes)
     int max_count = 0;   // capacity of the batch tables (capacity plans)
 
     template <typename T>

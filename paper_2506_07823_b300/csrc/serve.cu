@@ -32,7 +32,15 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-constexpr int kClasses = 2;  // nrob = 1, 2 (the sizes with a fused solver)
+// size classes nrob = 1, 2, 4, 8, 16 (class c holds 2^c robots, n = m = 12 nrob)
+constexpr int kClasses = 5;
+
+int class_of(int nrob)
+{
+    for (int c = 0; c < kClasses; ++c)
+        if (nrob == (1 << c)) return c;
+    return -1;
+}
 
 struct Entry {  // one request of a launch (device table)
     float *cx, *cu, *cl, *cxr, *cur;
@@ -199,6 +207,7 @@ private:
 
 struct pdilqr_server {
     pdilqr_serve_opts opts{};
+    pdilqr_srbd_model models[kClasses];   // constants per size class
     int device = 0;
     uint8_t* pool_base = nullptr;
     Pool pool;
@@ -271,23 +280,20 @@ pdilqr_status ensure_res(pdilqr_server* sv, Slot& sl, int cls)
 {
     ClassRes& r = sl.res[cls];
     if (r.ready) return PDILQR_OK;
-    const int nrob = cls + 1, n = 12 * nrob, nc = 4 * nrob;
+    const int nrob = 1 << cls, n = 12 * nrob, nc = 4 * nrob;
     const size_t B = sv->opts.max_batch, S = B * ((size_t)sv->opts.max_N + 1);
     r.n = n;
     r.nc = nc;
     // the largest warp count not above the requested one whose fused kernel
-    // fits in shared memory; sizes that fit with none run the requested count
-    // (clamped to the size's limit) from the global workspace
+    // fits in shared memory, else one chunk (the sequential sweep, from the
+    // global workspace): a chunk of a large state already fills its SM, so
+    // more chunks would only add the scan's extra work
     const SizeOps* ops = find_ops(n, n);
     if (!ops || !ops->sqp) return PDILQR_E_INVALID_ARG;
     auto smaller = [](int x) { return x == 16 ? 8 : (x == 8 ? 4 : 1); };
     int w = sv->opts.warps;
     while (w > 1 && (!warps_ok(ops, w) || ops->sqp_smem(w) > kSmemMax || ops->scan_gws_floats(w)))
         w = smaller(w);
-    if (ops->scan_gws_floats(w) || ops->sqp_smem(w) > kSmemMax) {
-        w = sv->opts.warps;
-        while (w > 1 && !warps_ok(ops, w)) w = smaller(w);
-    }
     pdilqr_status ps = plan_create_capacity(n, n, (int)B, (int64_t)S, w, &r.plan);
     if (ps != PDILQR_OK) return ps;
     cudaError_t e = cudaSuccess;
@@ -381,8 +387,8 @@ pdilqr_status launch_batch(pdilqr_server* sv, Slot& sl, std::vector<Request>& re
     if (cudaGetLastError() != cudaSuccess) return PDILQR_E_CUDA;
     ps = plan_set_batch_async(r.plan, r.hN, r.hoff, r.horder, count, maxN, st);
     if (ps != PDILQR_OK) return ps;
-    pdilqr_srbd_model md = sv->opts.model;
-    md.nrob = cls + 1;
+    pdilqr_srbd_model md = sv->models[cls];
+    md.nrob = 1 << cls;
     pdilqr_sqp_opts so{};
     so.max_iters = sv->opts.sqp_iters;
     so.tol_step = 0.f;
@@ -464,7 +470,7 @@ void worker_loop(pdilqr_server* sv)
         int cls = -1;
         for (const Request& q : sv->pending) {
             auto c = sv->clients.find(q.client);
-            if (c != sv->clients.end() && !c->second.busy) { cls = q.nrob - 1; break; }
+            if (c != sv->clients.end() && !c->second.busy) { cls = class_of(q.nrob); break; }
         }
         if (!sv->stop && free_slot && cls >= 0) {
             if (sv->opts.batch_window_us > 0 && (int)sv->pending.size() < sv->opts.max_batch) {
@@ -477,7 +483,7 @@ void worker_loop(pdilqr_server* sv)
                 auto cit = sv->clients.find(it->client);
                 if (cit == sv->clients.end()) { it = sv->pending.erase(it); continue; }
                 Client& c = cit->second;
-                if (it->nrob - 1 == cls && !c.busy) {
+                if (class_of(it->nrob) == cls && !c.busy) {
                     c.busy = true;
                     cl.push_back(&c);
                     reqs.push_back(std::move(*it));
@@ -533,6 +539,8 @@ extern "C" pdilqr_status pdilqr_serve_create(const pdilqr_serve_opts* o, pdilqr_
     pdilqr_server* sv = new (std::nothrow) pdilqr_server();
     if (!sv) return PDILQR_E_NO_MEMORY;
     sv->opts = *o;
+    for (int c = 0; c < kClasses; ++c) sv->models[c] = o->class_models ? o->class_models[c] : o->model;
+    sv->opts.class_models = nullptr;   // read here only
     if (sv->opts.hbm_budget_bytes <= 0) sv->opts.hbm_budget_bytes = int64_t(1) << 30;
     if (sv->opts.max_batch <= 0) sv->opts.max_batch = 1024;
     if (sv->opts.max_inflight <= 0) sv->opts.max_inflight = 2;
@@ -574,7 +582,7 @@ extern "C" pdilqr_status pdilqr_serve_submit(pdilqr_server* sv, uint64_t client_
                                              const pdilqr_request* q, uint64_t* ticket)
 {
     if (!sv || !q || !ticket || !q->x0hat) return PDILQR_E_INVALID_ARG;
-    if (q->nrob < 1 || q->nrob > kClasses || q->N < 1 || q->N > sv->opts.max_N)
+    if (class_of(q->nrob) < 0 || q->N < 1 || q->N > sv->opts.max_N)
         return PDILQR_E_INVALID_ARG;
     const bool refs = q->xref != nullptr;
     if (refs && (!q->uref || !q->contact)) return PDILQR_E_INVALID_ARG;

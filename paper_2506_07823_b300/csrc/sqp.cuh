@@ -152,43 +152,49 @@ struct LinArgs {
     const int64_t* off;
     const int64_t* stage_inst;
     int64_t total;
+    float* work;    // [blocks][StageL::SIZE] global stage areas, or null (shared memory)
 };
 
-// One warp per stage slot, four warps per block.
-template <int NX, int NU>
-__global__ void __launch_bounds__(128) linearize_kernel(const __grid_constant__ LinArgs a)
+// SPB stage slots per block, each linearised by a unit of UW warps into a
+// stage area in shared memory, or (work != null: stages larger than shared
+// memory) into the block's area of a global workspace; blocks stride over
+// the slots.
+template <int NX, int NU, int SPB, int UW>
+__global__ void __launch_bounds__(SPB * 32 * UW) linearize_kernel(const __grid_constant__ LinArgs a)
 {
     using L = StageL<NX, NU>;
+    constexpr int NT = 32 * UW;
     extern __shared__ __align__(16) float smem[];
-    const int warp = threadIdx.x >> 5;
-    const int64_t gs = (int64_t)blockIdx.x * 4 + warp;
-    if (gs >= a.total) return;
-    const int64_t inst = a.stage_inst[gs];
-    if (inst < 0) return;
-    const int N = a.N[inst];
-    const int k = (int)(gs - a.off[inst]);
-    const bool term = k == N;
-    const Grp<32> g{(int)(threadIdx.x & 31), 0};
-    float* st = smem + warp * L::SIZE;
+    const int unit = threadIdx.x / NT;
+    const Grp<NT> g{(int)(threadIdx.x % NT), 1 + unit};
+    float* st = a.work ? a.work + (int64_t)blockIdx.x * L::SIZE : smem + unit * L::SIZE;
     const int nrob = a.md.nrob;
-    srbd_linearize_stage<NX, NU, 32>(g, st, a.md, a.x + gs * NX, a.u + gs * NU,
-                                     term ? nullptr : a.x + (gs + 1) * NX, a.lam + gs * NX,
-                                     term ? nullptr : a.lam + (gs + 1) * NX, a.xref + gs * NX,
-                                     a.uref + gs * NU, a.contact + gs * 4 * nrob, term);
-    for (int e = g.t; e < NX * NX; e += 32) {
-        a.Q[gs * NX * NX + e] = st[L::Q + e];
-        a.A[gs * NX * NX + e] = term ? 0.f : st[L::A + e];
+    for (int64_t gs = (int64_t)blockIdx.x * SPB + unit; gs < a.total; gs += (int64_t)gridDim.x * SPB) {
+        const int64_t inst = a.stage_inst[gs];
+        if (inst < 0) continue;   // slot of no instance (uniform over the unit)
+        const int N = a.N[inst];
+        const int k = (int)(gs - a.off[inst]);
+        const bool term = k == N;
+        srbd_linearize_stage<NX, NU, NT>(g, st, a.md, a.x + gs * NX, a.u + gs * NU,
+                                         term ? nullptr : a.x + (gs + 1) * NX, a.lam + gs * NX,
+                                         term ? nullptr : a.lam + (gs + 1) * NX, a.xref + gs * NX,
+                                         a.uref + gs * NU, a.contact + gs * 4 * nrob, term);
+        for (int e = g.t; e < NX * NX; e += NT) {
+            a.Q[gs * NX * NX + e] = st[L::Q + e];
+            a.A[gs * NX * NX + e] = term ? 0.f : st[L::A + e];
+        }
+        for (int e = g.t; e < NX * NU; e += NT) {
+            a.B[gs * NX * NU + e] = term ? 0.f : st[L::B + e];
+            if (a.S) a.S[gs * NX * NU + e] = 0.f;
+        }
+        for (int e = g.t; e < NU * NU; e += NT) a.R[gs * NU * NU + e] = term ? 0.f : st[L::R + e];
+        for (int i = g.t; i < NX; i += NT) {
+            a.q[gs * NX + i] = st[L::q + i];
+            a.c[gs * NX + i] = term ? 0.f : st[L::c + i];
+        }
+        for (int i = g.t; i < NU; i += NT) a.r[gs * NU + i] = term ? 0.f : st[L::r + i];
+        g.sync();   // the stage area is rewritten by the next slot
     }
-    for (int e = g.t; e < NX * NU; e += 32) {
-        a.B[gs * NX * NU + e] = term ? 0.f : st[L::B + e];
-        if (a.S) a.S[gs * NX * NU + e] = 0.f;
-    }
-    for (int e = g.t; e < NU * NU; e += 32) a.R[gs * NU * NU + e] = term ? 0.f : st[L::R + e];
-    for (int i = g.t; i < NX; i += 32) {
-        a.q[gs * NX + i] = st[L::q + i];
-        a.c[gs * NX + i] = term ? 0.f : st[L::c + i];
-    }
-    for (int i = g.t; i < NU; i += 32) a.r[gs * NU + i] = term ? 0.f : st[L::r + i];
 }
 
 // ------------------------------------------------------ standalone merit

@@ -312,7 +312,11 @@ struct SrbdSource {
             stage_copy<NU, NT, true>(g.t, iur, uref + gs * NU);
             // contact flags: nrob words of 4 bytes (4-byte aligned per stage)
             const float* csrc = reinterpret_cast<const float*>(contact + gs * 4 * nrob);
-            for (int e = g.t; e < NX / 12; e += NT) cp_async4(reinterpret_cast<float*>(ict) + e, csrc + e);
+            for (int e = g.t; e < NX / 12; e += NT) {
+                float* d = reinterpret_cast<float*>(ict) + e;
+                if (__isShared(d)) cp_async4(d, csrc + e);
+                else *d = csrc[e];      // stage area in the global workspace
+            }
         }
         cp_async_commit();
         cp_async_wait_all();

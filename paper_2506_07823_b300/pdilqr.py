@@ -323,7 +323,10 @@ class _ServeOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("max_N", ctypes.c_int32),
                 ("sqp_iters", ctypes.c_int32), ("warps", ctypes.c_int32),
-                ("batch_window_us", ctypes.c_int32), ("model", SrbdModel)]
+                ("batch_window_us", ctypes.c_int32), ("model", SrbdModel),
+                ("class_models", ctypes.POINTER(SrbdModel))]
+
+SERVE_NROB = (1, 2, 4, 8, 16)   # the server's size classes (robots per client)
 
 
 class _Request(ctypes.Structure):
@@ -367,9 +370,17 @@ class Server:
 
     def __init__(self, model_params: dict, hbm_budget_bytes: int = 1 << 30, max_batch: int = 1024,
                  max_inflight: int = 2, max_N: int = 100, sqp_iters: int = 1, warps: int = 8,
-                 batch_window_us: int = 0):
+                 batch_window_us: int = 0, class_params: dict | None = None):
+        """``class_params`` optionally maps a robot count (1, 2, 4, 8, 16) to the
+        model constants of that class (formation offsets differ per count);
+        classes it does not name use ``model_params``."""
+        cm = None
+        if class_params is not None:
+            cm = (SrbdModel * len(SERVE_NROB))(
+                *[srbd_model(class_params.get(r, model_params)) for r in SERVE_NROB])
         o = _ServeOpts(int(hbm_budget_bytes), int(max_batch), int(max_inflight), int(max_N),
-                       int(sqp_iters), int(warps), int(batch_window_us), srbd_model(model_params))
+                       int(sqp_iters), int(warps), int(batch_window_us), srbd_model(model_params),
+                       ctypes.cast(cm, ctypes.POINTER(SrbdModel)) if cm is not None else None)
         h = _vp()
         _check(_lib.pdilqr_serve_create(ctypes.byref(o), ctypes.byref(h)), "pdilqr_serve_create")
         self._h = h

@@ -186,3 +186,31 @@ def test_two_size_classes_and_timeouts():
     # a client that never polls does not block shutdown
     submit(srv, 1, pr1, 1)
     srv.close()
+
+
+def test_large_classes_match_oracle():
+    """Clients of four and sixteen robots (n = 48 and 192), each class with its
+    own formation constants, next to single-robot clients."""
+    cls = {r: synth.srbd_params(r) for r in (1, 4, 16)}
+    srv = make_server(cls[1], class_params=cls, max_N=30)
+    r32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    cases = {40: (4, 12), 41: (16, 6), 42: (1, 30)}
+    probs = {c: synth.srbd_problem(N, seed=2000 + c, nrob=r) for c, (r, N) in cases.items()}
+    tickets = {c: srv.submit(c, r, N, probs[c]["x0hat"].astype(np.float32), probs[c]["xref"],
+                             probs[c]["uref"], probs[c]["contact"]) for c, (r, N) in cases.items()}
+    for c, (r, N) in cases.items():
+        res = srv.poll(tickets[c], n=12 * r, N=N, timeout_us=60_000_000)
+        assert res["status"] in (0, 8), (c, res["status"])
+        pr = probs[c]
+        x, u, lam, info = oracle.srbd_sqp(cls[r], r32(pr["x0hat"]),
+                                          np.tile(r32(pr["x0hat"]), (N + 1, 1)), r32(pr["uref"]),
+                                          np.zeros((N + 1, 12 * r)), r32(pr["xref"]), r32(pr["uref"]),
+                                          pr["contact"], max_iters=1)
+        assert rel(res["x"], x) <= REL_TOL, (c, rel(res["x"], x))
+        assert rel(res["u"][:-1], u[:-1]) <= REL_TOL, (c, rel(res["u"][:-1], u[:-1]))
+    from paper_2506_07823_b300 import pdilqr
+    with pytest.raises(pdilqr.PdilqrError) as e:
+        srv.submit(50, 3, 10, np.zeros(36, np.float32), np.zeros((11, 36), np.float32),
+                   np.zeros((11, 36), np.float32), np.zeros((11, 12), np.uint8))
+    assert e.value.code == pdilqr.E_INVALID_ARG
+    srv.close()

@@ -53,7 +53,7 @@ def dev(packed):
     return out
 
 
-@pytest.mark.parametrize("nrob", [1, 2])
+@pytest.mark.parametrize("nrob", [1, 2, 4, 8, 16])
 def test_linearize_parity(nrob):
     from paper_2506_07823_b300 import pdilqr
     n = 12 * nrob
@@ -189,3 +189,38 @@ def test_sqp_stops_on_tolerance():
     it = info["iters"].cpu().numpy()
     assert np.all(it < 30) and np.all(it >= 2), it
     assert np.all(info["status"].cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("warps", [1, 4])
+@pytest.mark.parametrize("nrob", [2, 4, 8, 16])
+def test_sqp_parity_multi_robot(nrob, warps):
+    """Centralised multi-robot problems (n = m = 12 nrob, ring formation cost)
+    through the fused SQP, replaying the oracle's step sizes; nrob >= 8 runs
+    its work areas from the global workspace."""
+    from paper_2506_07823_b300 import pdilqr
+    if nrob >= 8 and warps != 1:
+        pytest.skip("sizes beyond shared memory are served with one chunk")
+    n = 12 * nrob
+    Ns, iters = ([4, 7], 2) if nrob == 16 else ([6, 13], 3)
+    insts = [synth.srbd_problem(Ns[i], seed=500 + 10 * nrob + i, nrob=nrob) for i in range(2)]
+    packed, Nv, off = synth.pack(insts, synth.SRBD_KEYS)
+    x0 = np.stack([p["x0hat"] for p in insts])
+    prm = synth.srbd_params(nrob)
+    refs = [run_oracle(prm, pr, iters) for pr in insts]
+    d = dev(packed)
+    plan = pdilqr.Plan(n, n, Nv, off, warps=warps)
+    replay = torch.tensor(np.stack([r[3]["alpha"] for r in refs]).astype(np.float32), device="cuda")
+    info = plan.solve(pdilqr.srbd_model(prm), torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                      d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                      max_iters=iters, alpha_replay=replay)
+    torch.cuda.synchronize()
+    assert np.all(info["status"].cpu().numpy() == 0)
+    assert np.all(info["iters"].cpu().numpy() == iters)
+    xs, us, ls = (d[k].double().cpu().numpy() for k in ("x", "u", "lam"))
+    for i, (xr, ur, lr, inf) in enumerate(refs):
+        N, o = int(Nv[i]), int(off[i])
+        sl = slice(o, o + N + 1)
+        assert rel(xs[sl], xr) <= REL_TOL, rel(xs[sl], xr)
+        assert rel(us[o:o + N], ur[:N]) <= REL_TOL, rel(us[o:o + N], ur[:N])
+        assert rel(ls[sl], lr) <= REL_TOL, rel(ls[sl], lr)
+        assert abs(info["J"][i].item() - inf["J"]) <= 1e-4 * abs(inf["J"])
