@@ -49,7 +49,7 @@ typedef struct CUstream_st *pdilqr_stream; /* == cudaStream_t */
 typedef enum {
     PDILQR_OK = 0,
     PDILQR_E_INVALID_ARG = 1,  /* bad size, null pointer, unsupported (n, m)      */
-    PDILQR_E_NOT_SPD = 2,      /* a Cholesky pivot of R_k or G_k was not positive */
+    PDILQR_E_NOT_SPD = 2,      /* a pivot of R_k or G_k (an SPD factorisation) was not positive */
     PDILQR_E_SINGULAR = 3,     /* a pivot of (I + C P) vanished in a combine      */
     PDILQR_E_NONFINITE = 4,    /* NaN / Inf met                                    */
     PDILQR_E_TIMEOUT = 5,      /* a bounded device or host wait ran out            */

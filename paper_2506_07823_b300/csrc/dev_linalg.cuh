@@ -497,6 +497,54 @@ __device__ bool gj_warp(int lane, float* G, int ld, float* colbuf)
     return ok;
 }
 
+// G^-1 X for an SPD M x M matrix G and NR right-hand sides X (M x NR) by
+// Gauss-Jordan elimination without pivoting, one column per lane in registers:
+// lane j < M holds column j of G, lane M + r holds right-hand side r.  For an
+// SPD matrix the pivots are the diagonal of its L D L^T factorisation, so
+// "every pivot positive and finite" is the SPD test (the one a Cholesky
+// factorisation makes) and no pivot search is needed.  Step k: lane k
+// publishes its column (double-buffered shared slot), every lane scales its
+// row-k entry and eliminates.  Out (M x NR) receives G^-1 X; every operand is
+// read before anything is written, so Out may alias X.  colbuf: 2 M floats.
+// Returns false (uniformly over the warp) if a pivot is not positive and finite.
+template <int M, int NR>
+__device__ bool spd_solve_warp(int lane, const float* G, int ldg, const float* X, int ldx,
+                               float* Out, int ldo, float* colbuf)
+{
+    static_assert(M + NR <= 32, "one column per lane");
+    const bool isG = lane < M;
+    const bool isX = lane >= M && lane < M + NR;
+    float c[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) c[i] = isG ? G[i * ldg + lane] : (isX ? X[i * ldx + lane - M] : 0.f);
+    __syncwarp();
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        // a slot is rewritten two steps later, after every lane has passed
+        // the next step's barrier (and so finished reading this one)
+        float* cb = colbuf + (k & 1) * M;
+        if (lane == k) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) cb[i] = c[i];
+        }
+        __syncwarp();
+        const float pk = cb[k];
+        ok = ok && (pk > 0.f) && isfinite(pk);
+        const float r = c[k] * rcp_approx(pk);
+        c[k] = r;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (i != k) c[i] = fmaf(-cb[i], r, c[i]);
+    }
+    if (isX) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) Out[i * ldo + lane - M] = c[i];
+    }
+    __syncwarp();
+    return ok;
+}
+
 // ---------------------------------------------------------------- dispatch
 // One-warp groups use the register versions (they need a small shared
 // scratch: `wsc`, at least 2 * (max(M, N) + 3) floats); wider groups use the

@@ -26,7 +26,10 @@
 //   A = A2 M^-1 A1,            b = A2 M^-1 (b1 - C1 p2) + b2,
 //   C = A2 M^-1 C1 A2^T + C2,  P = (M^-1 A1)^T P2 A1 + P1,
 //   p = (M^-1 A1)^T (p2 + P2 b1) + p1,
-// with M^-1 applied by Gauss-Jordan elimination with partial pivoting.
+// with M^-1 applied by Gauss-Jordan elimination with partial pivoting (one
+// warp: M^-1 itself from [M | I], then products).  The SPD systems of the
+// element build (R) and the Riccati step (G) are solved by elimination
+// without pivoting, whose positive pivots are the SPD test.
 #pragma once
 
 #include "dev_linalg.cuh"
@@ -82,7 +85,23 @@ template <int NX>
 struct CombL {  // scratch of a combine
     static constexpr int LDG = 3 * NX + 1;
     static constexpr int G = 0, T = round4(NX * LDG), U = T + NX * NX, w = U + NX * NX,
-                         Wk = round4(w + NX), SIZE = round4(Wk + 3 * (NX + 1));
+                         Wk = round4(w + NX), SIZE0 = round4(Wk + 3 * (NX + 1));
+    // one-warp full combine through M^-1: [M | I] (T reuses its area once
+    // M^-1 has been applied), M^-1 A1, M^-1 C1, b1 - C1 p2 and M^-1 of it
+    static constexpr int LDI = 2 * NX;
+    static constexpr int GI = 0, XA = round4(NX * LDI), XC = XA + NX * NX, UI = XC + NX * NX,
+                         wI = UI + NX * NX, xb = round4(wI + NX), vb = round4(xb + NX),
+                         WkI = round4(vb + NX), SIZE1 = round4(WkI + 3 * (NX + 1));
+    static constexpr int SIZE = SIZE0 > SIZE1 ? SIZE0 : SIZE1;
+};
+
+// One-warp fast paths: SPD solves by Gauss-Jordan without pivoting when
+// [G | H | h] fits one column per lane; the full combine through M^-1 when
+// [M | I] does.
+template <int NX, int NU, int NT>
+struct WarpPath {
+    static constexpr bool spd = NT == 32 && NU + NX + 1 <= 32;
+    static constexpr bool inv = NT == 32 && 2 * NX <= 32;
 };
 
 template <int NX, int NU>
@@ -160,6 +179,24 @@ __device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float
     float* Z = scr + S::Z;
     float* Y = scr + S::Y;
     constexpr int LDY = NX + 1;
+    if constexpr (WarpPath<NX, NU, NT>::spd) {
+        if (!has_S) {
+            // [X | y] = R^-1 [B^T | r] in one elimination;  C = B X,  b = c - B y
+            copy<NU, NX, true, NT, false>(g, Y, LDY, st + L::B, NU);
+            for (int i = g.t; i < NU; i += NT) Y[i * LDY + NX] = st[L::r + i];
+            g.sync();
+            const bool ok = spd_solve_warp<NU, NX + 1>(g.t, st + L::R, NU, Y, LDY, Y, LDY, scr + S::Wk);
+            mm<NX, NX, NU, false, false, NT, false>(g, e + E::C, NX, st + L::B, NU, Y, LDY);
+            mm<NX, 1, NU, false, false, NT, false>(g, e + E::b, 1, st + L::B, NU, Y + NX, LDY,
+                                                   st + L::c, 1, -1.f);
+            copy<NX, NX, false, NT, false>(g, e + E::A, NX, st + L::A, NX);
+            copy<NX, NX, false, NT, false>(g, e + E::P, NX, st + L::Q, NX);
+            for (int i = g.t; i < NX; i += NT) e[E::p + i] = st[L::q + i];
+            g.sync();
+            symmetrize<NX, NT>(g, e + E::C, NX);
+            return ok;
+        }
+    }
     copy<NU, NU, false, NT, false>(g, Lr, NU, st + L::R, NU);
     copy<NU, NX, true, NT, false>(g, Z, NX, st + L::B, NU);   // Z = B^T
     if (has_S) copy<NU, NX, false, NT, false>(g, Y, LDY, st + L::S, NX);
@@ -202,6 +239,44 @@ __device__ bool combine_full(const Grp<NT>& g, const float* e1, const float* e2,
 {
     using E = ElemL<NX>;
     using S = CombL<NX>;
+    if constexpr (WarpPath<NX, NX, NT>::inv) {
+        // one warp: M^-1 by Gauss-Jordan on [M | I] (one column per lane),
+        // then X_A = M^-1 A1, X_C = M^-1 C1, x_b = M^-1 (b1 - C1 p2) by products
+        constexpr int LD = S::LDI;
+        float* G = scr + S::GI;
+        float* XA = scr + S::XA;
+        float* XC = scr + S::XC;
+        float* U = scr + S::UI;
+        float* w = scr + S::wI;
+        float* xb = scr + S::xb;
+        float* vb = scr + S::vb;
+        float* T = scr + S::GI;   // written once M^-1 is no longer read
+        mm<NX, NX, NX, false, false, NT, false>(g, G, LD, e1 + E::C, NX, e2 + E::P, NX);
+        fill<NX, NX, NT, false>(g, G + NX, LD, 0.f, 1.f);
+        mm<NX, 1, NX, false, false, NT, false>(g, vb, 1, e1 + E::C, NX, e2 + E::p, 1, e1 + E::b, 1,
+                                               -1.f);
+        mm<NX, NX, NX, false, false, NT, false>(g, U, NX, e2 + E::P, NX, e1 + E::A, NX);
+        mm<NX, 1, NX, false, false, NT, false>(g, w, 1, e2 + E::P, NX, e1 + E::b, 1, e2 + E::p, 1);
+        g.sync();
+        for (int i = g.t; i < NX; i += NT) G[i * LD + i] += 1.f;   // M = I + C1 P2
+        g.sync();
+        const bool ok = gj_warp<NX, NX>(g.t, G, LD, scr + S::WkI);
+        const float* Mi = G + NX;
+        mm<NX, NX, NX, false, false, NT, false>(g, XA, NX, Mi, LD, e1 + E::A, NX);
+        mm<NX, NX, NX, false, false, NT, false>(g, XC, NX, Mi, LD, e1 + E::C, NX);
+        mm<NX, 1, NX, false, false, NT, false>(g, xb, 1, Mi, LD, vb, 1);
+        g.sync();
+        mm<NX, NX, NX, false, false, NT, false>(g, out + E::A, NX, e2 + E::A, NX, XA, NX);
+        mm<NX, 1, NX, false, false, NT, false>(g, out + E::b, 1, e2 + E::A, NX, xb, 1, e2 + E::b, 1);
+        mm<NX, NX, NX, false, false, NT, false>(g, T, NX, e2 + E::A, NX, XC, NX);
+        mm<NX, NX, NX, true, false, NT, false>(g, out + E::P, NX, XA, NX, U, NX, e1 + E::P, NX);
+        mm<NX, 1, NX, true, false, NT, false>(g, out + E::p, 1, XA, NX, w, 1, e1 + E::p, 1);
+        g.sync();
+        mm<NX, NX, NX, false, true, NT>(g, out + E::C, NX, T, NX, e2 + E::A, NX, e2 + E::C, NX);
+        symmetrize<NX, NT, false>(g, out + E::C, NX);
+        symmetrize<NX, NT>(g, out + E::P, NX);
+        return ok;
+    }
     constexpr int LDG = S::LDG;
     float* G = scr + S::G;
     float* T = scr + S::T;
@@ -268,9 +343,11 @@ __device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, f
 //   G = R + B^T P' B,  H = S + B^T P' A,  h = B^T (p' + P' c) + r,
 //   K = -G^-1 H,  k = -G^-1 h,
 //   P = Q + A^T P' A + K^T H,  p = q + A^T (p' + P' c) + K^T h,
-// using the Cholesky factor G = L L^T: with [Z | z] = L^-1 [H | h],
-// K^T H = -Z^T Z and K^T h = -Z^T z.  Writes P, p into vout (SMEM) and K, k,
-// P, p, Abar = A + B K, bbar = B k + c to global memory at stage gs.
+// with G^-1 [H | h] from one SPD elimination without pivoting (one warp,
+// K^T [H | h] = -(G^-1 H)^T [H | h]) or, for wider systems, from the Cholesky
+// factor G = L L^T: with [Z | z] = L^-1 [H | h], K^T H = -Z^T Z and
+// K^T h = -Z^T z.  Writes P, p into vout (SMEM) and K, k, P, p,
+// Abar = A + B K, bbar = B k + c to global memory at stage gs.
 template <int NX, int NU, int NT>
 __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin, float* vout,
                              float* scr, const KktArgs& a, int64_t gs, bool has_S)
@@ -297,18 +374,28 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
                                            has_S ? st + L::S : nullptr, NX);
     mm<NU, 1, NX, true, false, NT, false>(g, Y + NX, LDY, st + L::B, NU, w, 1, st + L::r, 1);
     g.sync();
-    const bool ok = chol<NU, NT>(g, Gm, NU, dinv, scr + S::Wk);
-    trsm_lower<NU, NX + 1, NT>(g, Gm, NU, dinv, Y, LDY);           // [Z | z]
-    copy<NU, NX + 1, false, NT>(g, Y2, LDY, Y, LDY);
-    trsm_lower_t<NU, NX + 1, NT>(g, Gm, NU, dinv, Y2, LDY);        // G^-1 [H | h]
-    // P = Q + A^T (P' A) - Z^T Z ;  p = q + A^T w - Z^T z
+    // Y2 = G^-1 [H | h];  Yr = the factor paired with Y in K^T [H | h]:
+    // G^-1 [H | h] itself (SPD elimination, Y untouched) or, after a Cholesky
+    // factorisation G = L L^T, Y = L^-1 [H | h] paired with itself
+    constexpr bool SPD = WarpPath<NX, NU, NT>::spd;
+    bool ok;
+    if constexpr (SPD) {
+        ok = spd_solve_warp<NU, NX + 1>(g.t, Gm, NU, Y, LDY, Y2, LDY, scr + S::Wk);
+    } else {
+        ok = chol<NU, NT>(g, Gm, NU, dinv, scr + S::Wk);
+        trsm_lower<NU, NX + 1, NT>(g, Gm, NU, dinv, Y, LDY);           // [Z | z]
+        copy<NU, NX + 1, false, NT>(g, Y2, LDY, Y, LDY);
+        trsm_lower_t<NU, NX + 1, NT>(g, Gm, NU, dinv, Y2, LDY);        // G^-1 [H | h]
+    }
+    const float* Yr = SPD ? Y2 : Y;
+    // P = Q + A^T (P' A) + K^T H ;  p = q + A^T w + K^T h
     float* P = vout + E::P;
     float* p = vout + E::p;
     mm<NX, NX, NX, true, false, NT, false>(g, P, NX, st + L::A, NX, PA, NX, st + L::Q, NX);
     mm<NX, 1, NX, true, false, NT, false>(g, p, 1, st + L::A, NX, w, 1, st + L::q, 1);
     g.sync();
-    mm<NX, NX, NU, true, false, NT, false>(g, P, NX, Y, LDY, Y, LDY, P, NX, -1.f);
-    mm<NX, 1, NU, true, false, NT, false>(g, p, 1, Y, LDY, Y + NX, LDY, p, 1, -1.f);
+    mm<NX, NX, NU, true, false, NT, false>(g, P, NX, Y, LDY, Yr, LDY, P, NX, -1.f);
+    mm<NX, 1, NU, true, false, NT, false>(g, p, 1, Y, LDY, Yr + NX, LDY, p, 1, -1.f);
     // K = -Y2[:, :NX], k = -Y2[:, NX];  Abar = A + B K;  bbar = B k + c
     float* Kg = a.K + gs * NU * NX;
     float* kg = a.k + gs * NU;
