@@ -399,6 +399,30 @@ def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args):
         t = event_times(torch, g.replay, reps, stream)
         lat[name + "_p50"] = pct(t, 50)
         lat[name + "_p99"] = pct(t, 99)
+    # the same batch through the sequential recursion: the fused SQP with one
+    # horizon chunk per instance (one warp, 16 CTAs per SM)
+    p1 = pdilqr.Plan(12, 12, plan.N, plan.stage_off, warps=1)
+    inf1 = {"iters": torch.zeros(p1.count, device=dev, dtype=torch.int32),
+            "status": torch.zeros(p1.count, device=dev, dtype=torch.int32),
+            "alpha": None, "J": None, "theta": None}
+
+    def ric_batch():
+        p1.solve(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"], work["uref"],
+                 work["contact"], max_iters=ITERS, info=inf1)
+
+    def reset_work():
+        for k in ("x", "u", "lam"):
+            work[k].copy_(base[k], non_blocking=True)
+    reset_work()
+    ric_batch()
+    torch.cuda.synchronize()
+    t = event_times(torch, ric_batch, 3, stream, before=reset_work)
+    comp["riccati_sqp_batched"] = {
+        "kkt_solves_per_s": float(inf1["iters"].sum().item()) / (np.mean(t) / 1e3),
+        "ms": float(np.mean(t)), "warps_per_instance": 1,
+        "note": "same 4096-instance batch and fused SQP kernel, one horizon chunk per instance "
+                "(the sequential Riccati recursion)"}
+    p1.close()
     # LQ KKT solves alone on the linearisation of the 4096-instance batch
     lq = plan.linearize(md, base)
     lq["S"] = None
@@ -621,6 +645,64 @@ def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, w
             "streams": inflight}
 
 
+# ------------------------------------------------------- horizon sweep
+def run_sweep(args):
+    """Single-instance latency of one SQP iteration (linearisation, LQ KKT
+    solve, line search, update; CUDA-graph replays) against the horizon N
+    (one robot) and against the robot count R of a centralised problem
+    (n = m = 12 R, N = 50), for the scan and for the sequential recursion."""
+    import torch
+    from paper_2506_07823_b300 import pdilqr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    reps = args.latency_reps
+
+    def latency(nrob, N, warps):
+        prm = synth.srbd_params(nrob)
+        md = pdilqr.srbd_model(prm)
+        pr = synth.srbd_problem(N, seed=SEED, nrob=nrob)
+        pk, Nv, off = synth.pack([pr], synth.SRBD_KEYS)
+        one = build_device_batch(torch, [pr], pk, Nv, off, pr["x0hat"][None], dev)
+        w = {k: v.clone() for k, v in one.items()}
+        n = 12 * nrob
+        p = pdilqr.Plan(n, n, Nv, off, warps=warps)
+        inf = {"iters": torch.zeros(1, device=dev, dtype=torch.int32),
+               "status": torch.zeros(1, device=dev, dtype=torch.int32),
+               "alpha": None, "J": None, "theta": None}
+
+        def step():
+            for k in ("x", "u", "lam"):
+                w[k].copy_(one[k], non_blocking=True)
+            p.solve(md, w["x0hat"], w["x"], w["u"], w["lam"], w["xref"], w["uref"], w["contact"],
+                    max_iters=1, info=inf)
+        step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(5):
+            g.replay()
+        t = event_times(torch, g.replay, reps, stream)
+        used = p.warps
+        p.close()
+        return {"p50_ms": pct(t, 50), "p99_ms": pct(t, 99), "warps": used}
+
+    horizon = []
+    for N in (25, 50, 100, 150, 200):
+        sc, ri = latency(1, N, 16), latency(1, N, 1)
+        horizon.append({"N": N, "scan": sc, "riccati": ri,
+                        "speedup_p50": ri["p50_ms"] / sc["p50_ms"]})
+    robots = []
+    for R in (1, 2, 4, 8, 16):
+        sc, ri = latency(R, 50, 0), latency(R, 50, 1)
+        robots.append({"robots": R, "n": 12 * R, "scan": sc, "riccati": ri,
+                       "speedup_p50": ri["p50_ms"] / sc["p50_ms"]})
+    return {"sweep": "one SQP iteration, single instance, CUDA-graph replays",
+            "horizon_n12": horizon, "robots_N50": robots,
+            "work_ratio_scan_to_riccati": "about 50 n^3 vs 13 n^3 flop per stage (n = m)"}
+
+
 # --------------------------------------------------------- reference arm
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -670,9 +752,14 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (1/s)")
     ap.add_argument("--no-lq-workloads", dest="lq_workloads", action="store_false",
                     help="skip the whole-body LQ batch and single-LQR measurements")
+    ap.add_argument("--sweep", action="store_true",
+                    help="print the horizon / robot-count latency sweep instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.sweep:
+        print(json.dumps(run_sweep(args)), flush=True)
+        return
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:
         print(json.dumps(res), flush=True)
