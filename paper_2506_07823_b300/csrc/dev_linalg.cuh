@@ -81,6 +81,7 @@ template <int NT>
 struct Grp {
     int t;    // rank inside the group
     int bar;  // named barrier id (groups wider than one warp)
+    float* tb = nullptr;  // the group's shared-memory tile buffer (TileBuf), or none
     __device__ __forceinline__ void sync() const {
         if constexpr (NT == 32) {
             __syncwarp();
@@ -113,6 +114,132 @@ struct TilePick {
     static constexpr int CT = pick() % 8;
 };
 
+// Opt-in dynamic shared memory of one CTA on sm_103a.
+constexpr size_t kSmemCta = 227 * 1024;
+
+// Tile buffer of a wide group's shared-memory tiled product: a K-chunk of
+// op(A) (BK x BM, k-major) and of op(B) (BK x BN), rows padded to LDT.
+struct TileBuf {
+    static constexpr int BM = 64, BN = 64, BK = 32, LDT = 68;
+    static constexpr int FLOATS = 2 * BK * LDT;
+};
+
+// out[R][C] = D + sgn * op(A) op(B) for a group of NT = 128 or 256 threads
+// through its tile buffer: 64 x 64 output tiles; per K-chunk of 32 the group
+// copies op(A) and op(B) into shared memory (coalesced along the operands'
+// contiguous index, zero-filled beyond the edges), then every thread
+// accumulates a 4 x TC register tile from float4 reads.  Operands may live in
+// global or shared memory; out may alias D but not A or B.
+template <int R, int C, int K, bool TA, bool TB, int NT>
+__device__ void mm_tiled(const Grp<NT>& g, float* out, int ldo, const float* A, int lda,
+                         const float* B, int ldb, const float* D, int ldd, float sgn)
+{
+    static_assert(NT == 128 || NT == 256, "tiled product groups");
+    constexpr int BM = TileBuf::BM, BN = TileBuf::BN, BK = TileBuf::BK, LDT = TileBuf::LDT;
+    constexpr int TC = BM * BN / (NT * 4);   // 4 (NT = 256) or 8 (NT = 128) columns
+    constexpr int CG = BN / TC;              // column groups
+    float* As = g.tb;
+    float* Bs = g.tb + BK * LDT;
+    const int tx = g.t % CG, ty = g.t / CG;
+    for (int r0 = 0; r0 < R; r0 += BM) {
+        for (int c0 = 0; c0 < C; c0 += BN) {
+            float acc[4][TC];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) acc[i][j] = 0.f;
+            // K-chunks: every load of a chunk is issued before its first
+            // shared store (through generic pointers the compiler cannot
+            // order them otherwise), then the chunk is multiplied
+            constexpr int NL = BM * BK / NT;
+            for (int k0 = 0; k0 < K; k0 += BK) {
+                {
+                    float va[NL];
+#pragma unroll
+                    for (int q = 0; q < NL; ++q) {
+                        // As[l][r] = op(A)(r0 + r, k0 + l)
+                        const int e = g.t + q * NT;
+                        const int r = TA ? e % BM : e / BK, l = TA ? e / BM : e % BK;
+                        const int gr = r0 + r, gl = k0 + l;
+                        va[q] = ((R % BM == 0 || gr < R) && (K % BK == 0 || gl < K))
+                                    ? (TA ? A[(size_t)gl * lda + gr] : A[(size_t)gr * lda + gl]) : 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < NL; ++q) {
+                        const int e = g.t + q * NT;
+                        const int r = TA ? e % BM : e / BK, l = TA ? e / BM : e % BK;
+                        As[l * LDT + r] = va[q];
+                    }
+                }
+                {
+                    float vb[NL];
+#pragma unroll
+                    for (int q = 0; q < NL; ++q) {
+                        // Bs[l][c] = op(B)(k0 + l, c0 + c)
+                        const int e = g.t + q * NT;
+                        const int c = TB ? e / BK : e % BN, l = TB ? e % BK : e / BN;
+                        const int gc = c0 + c, gl = k0 + l;
+                        vb[q] = ((C % BN == 0 || gc < C) && (K % BK == 0 || gl < K))
+                                    ? (TB ? B[(size_t)gc * ldb + gl] : B[(size_t)gl * ldb + gc]) : 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < NL; ++q) {
+                        const int e = g.t + q * NT;
+                        const int c = TB ? e / BK : e % BN, l = TB ? e % BK : e / BN;
+                        Bs[l * LDT + c] = vb[q];
+                    }
+                }
+                g.sync();
+#pragma unroll 8
+                for (int l = 0; l < BK; ++l) {
+                    const float4 a = *reinterpret_cast<const float4*>(As + l * LDT + ty * 4);
+                    float b[TC];
+#pragma unroll
+                    for (int q = 0; q < TC / 4; ++q) {
+                        const float4 bq = *reinterpret_cast<const float4*>(Bs + l * LDT + tx * TC + 4 * q);
+                        b[4 * q] = bq.x; b[4 * q + 1] = bq.y; b[4 * q + 2] = bq.z; b[4 * q + 3] = bq.w;
+                    }
+                    const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(av[i], b[j], acc[i][j]);
+                }
+                g.sync();
+            }
+            // addends first, then the stores (out may alias D)
+            if (D) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = r0 + ty * 4 + i;
+#pragma unroll
+                    for (int j = 0; j < TC; ++j) {
+                        const int c = c0 + tx * TC + j;
+                        const bool in = (R % BM == 0 || r < R) && (C % BN == 0 || c < C);
+                        acc[i][j] = sgn * acc[i][j] + (in ? D[(size_t)r * ldd + c] : 0.f);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < TC; ++j) acc[i][j] *= sgn;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = r0 + ty * 4 + i;
+                if (R % BM != 0 && r >= R) continue;
+#pragma unroll
+                for (int j = 0; j < TC; ++j) {
+                    const int c = c0 + tx * TC + j;
+                    if (C % BN != 0 && c >= C) continue;
+                    out[(size_t)r * ldo + c] = acc[i][j];
+                }
+            }
+        }
+    }
+}
+
 // out[R][C] = D + sgn * op(A) op(B)   (D == nullptr: no addend)
 // op(A)(r,l) = TA ? A[l*lda + r] : A[r*lda + l];  op(B)(l,c) likewise.
 // out must not alias A or B; it may alias D.
@@ -121,6 +248,14 @@ __device__ __forceinline__ void mm(const Grp<NT>& g, float* out, int ldo,
                                    const float* A, int lda, const float* B, int ldb,
                                    const float* D = nullptr, int ldd = 0, float sgn = 1.f)
 {
+    // wide groups with a tile buffer take large products through shared memory
+    if constexpr ((NT == 128 || NT == 256) && R >= 48 && C >= 48 && K >= 32) {
+        if (g.tb) {
+            mm_tiled<R, C, K, TA, TB, NT>(g, out, ldo, A, lda, B, ldb, D, ldd, sgn);
+            if constexpr (SYNC) g.sync();
+            return;
+        }
+    }
     constexpr int RT = TilePick<R, C, NT>::RT, CT = TilePick<R, C, NT>::CT;
     constexpr int TR = cdiv(R, RT), TC = cdiv(C, CT), NTILE = TR * TC;
     for (int tile = g.t; tile < NTILE; tile += NT) {
@@ -148,6 +283,17 @@ __device__ __forceinline__ void mm(const Grp<NT>& g, float* out, int ldo,
 #pragma unroll
                 for (int j = 0; j < CT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
+        // addends first, then the stores (out may alias D)
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+            const int r = r0 + i;
+#pragma unroll
+            for (int j = 0; j < CT; ++j) {
+                const int c = c0 + j;
+                const bool in = (R % RT == 0 || r < R) && (C % CT == 0 || c < C);
+                acc[i][j] = sgn * acc[i][j] + ((D && in) ? D[r * ldd + c] : 0.f);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
             const int r = r0 + i;
@@ -156,9 +302,7 @@ __device__ __forceinline__ void mm(const Grp<NT>& g, float* out, int ldo,
             for (int j = 0; j < CT; ++j) {
                 const int c = c0 + j;
                 if (C % CT != 0 && c >= C) continue;
-                float v = sgn * acc[i][j];
-                if (D) v += D[r * ldd + c];
-                out[r * ldo + c] = v;
+                out[r * ldo + c] = acc[i][j];
             }
         }
     }
@@ -272,43 +416,92 @@ __device__ void trsm_lower_t_generic(const Grp<NT>& g, const float* L, int ld, c
 }
 
 // Gauss-Jordan elimination with partial pivoting on the augmented matrix
-// [Mx | RHS] (Mx is N x N in columns 0..N-1, NR right-hand sides after it).
-// On exit columns N..N+NR-1 hold Mx^{-1} RHS.  Returns false (uniformly) if
-// a pivot is zero or not finite.
+// [Mx | RHS] (Mx is N x N in columns 0..N-1, NR right-hand sides after it)
+// by a group of NT threads, one column per thread.  Step k exchanges rows k
+// and p (the pivot row) and eliminates column k from every other row, over
+// the columns right of the pivot; column k itself is read but never written
+// in the step (the exchange is applied to it virtually), and the pivot row
+// is not normalised, so one barrier per step suffices.  The thread that
+// updates column k + 1 also finds the next pivot row and publishes the
+// column as the next step's multipliers in the group's tile buffer
+// (double-buffered; without one the multipliers are read from column k).
+// Columns are processed in register chunks of rows.  On exit columns
+// N..N+NR-1 hold Mx^{-1} RHS (each row divided by its pivot).  wsc: 2 N
+// floats.  Returns false (uniformly) if a pivot is zero or not finite.
 template <int N, int NR, int NT>
-__device__ bool gj_solve_generic(const Grp<NT>& g, float* G, int ld)
+__device__ bool gj_solve_generic(const Grp<NT>& g, float* G, int ld, float* wsc)
 {
     constexpr int W = N + NR;
+    constexpr int RB = 12;
+    int* prow = reinterpret_cast<int*>(wsc);   // [N] pivot rows
+    float* dpiv = wsc + N;                     // [N] pivots
+    float* mbuf = (g.tb && 2 * N <= TileBuf::FLOATS) ? g.tb : nullptr;
+    if (mbuf)
+        for (int i = g.t; i < N; i += NT) mbuf[i] = G[(size_t)i * ld];
+    if (g.t == 0) {
+        int bi = 0;
+        float best = -1.f;
+        for (int i = 0; i < N; ++i) {
+            const float v = fabsf(G[(size_t)i * ld]);
+            if (v > best) { best = v; bi = i; }
+        }
+        prow[0] = bi;
+    }
+    g.sync();
     bool ok = true;
     for (int k = 0; k < N; ++k) {
-        int piv = k;
-        float best = fabsf(G[k * ld + k]);
-        for (int i = k + 1; i < N; ++i) {
-            const float v = fabsf(G[i * ld + k]);
-            if (v > best) { best = v; piv = i; }
-        }
-        ok = ok && (best > 1e-30f) && isfinite(best);
-        if (piv != k) {  // uniform: every thread saw the same column
-            g.sync();
-            for (int j = k + g.t; j < W; j += NT) {
-                const float a = G[k * ld + j];
-                G[k * ld + j] = G[piv * ld + j];
-                G[piv * ld + j] = a;
+        const float* mc = mbuf ? mbuf + (k & 1) * N : nullptr;   // column k
+        float* mnext = mbuf ? mbuf + ((k + 1) & 1) * N : nullptr;
+        const int p = prow[k];
+        const float dk = mc ? mc[p] : G[(size_t)p * ld + k];
+        ok = ok && (fabsf(dk) > 1e-30f) && isfinite(dk);
+        const float idk = 1.f / dk;
+        const float mk = mc ? mc[k] : G[(size_t)k * ld + k];   // multiplier of row p after the exchange
+        for (int j = k + 1 + g.t; j < W; j += NT) {
+            float* col = G + j;
+            const float vk = col[(size_t)p * ld], vp = col[(size_t)k * ld];
+            col[(size_t)k * ld] = vk;             // pivot row
+            const float rk = vk * idk;
+            const bool next = (j == k + 1);
+            const bool pub = mnext && next && j < N;
+            float best = -1.f;
+            int bi = k + 1;
+            // rows in batches: every load of a batch (multipliers from the
+            // staged column when present) is issued before the batch's stores
+            for (int i0 = 0; i0 < N; i0 += RB) {
+                float mv[RB], cv[RB];
+#pragma unroll
+                for (int q = 0; q < RB; ++q) {
+                    const int i = i0 + q;
+                    const bool in = N % RB == 0 || i < N;
+                    mv[q] = in ? (mc ? mc[i] : G[(size_t)i * ld + k]) : 0.f;
+                    cv[q] = in ? col[(size_t)i * ld] : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < RB; ++q) {
+                    const int i = i0 + q;
+                    if (N % RB == 0 || i < N) {
+                        // the pivot row keeps vk (stored again with the same
+                        // value), row p takes the exchanged row k's entry
+                        const bool ik = (i == k), ip = (i == p) && !ik;
+                        const float u = fmaf(-(ip ? mk : mv[q]), rk, ip ? vp : cv[q]);
+                        const float v = ik ? vk : u;
+                        col[(size_t)i * ld] = v;
+                        if (pub) mnext[i] = v;
+                        if (next && i > k && fabsf(v) > best) { best = fabsf(v); bi = i; }
+                    }
+                }
             }
-            g.sync();
+            if (next && k + 1 < N) prow[k + 1] = bi;
         }
-        const float inv = 1.f / G[k * ld + k];
-        for (int j = k + 1 + g.t; j < W; j += NT) G[k * ld + j] *= inv;
-        g.sync();
-        const int cols = W - k - 1;
-        for (int e = g.t; e < (N - 1) * cols; e += NT) {
-            const int ii = e / cols;
-            const int i = ii + (ii >= k ? 1 : 0);
-            const int j = k + 1 + e % cols;
-            G[i * ld + j] -= G[i * ld + k] * G[k * ld + j];
-        }
+        if (g.t == 0) dpiv[k] = dk;
         g.sync();
     }
+    for (int e = g.t; e < N * NR; e += NT) {
+        const int i = e / NR, c = e - i * NR;
+        G[(size_t)i * ld + N + c] *= 1.f / dpiv[i];
+    }
+    g.sync();
     return ok;
 }
 
@@ -545,6 +738,76 @@ __device__ bool spd_solve_warp(int lane, const float* G, int ldg, const float* X
     return ok;
 }
 
+// G^-1 X for an SPD M x M matrix G (overwritten) and NR right-hand sides X
+// (overwritten by the solution) by a group of NT threads: Gauss-Jordan
+// elimination without pivoting, one column of [G | X] per thread.  Step k
+// subtracts G[i][k] / G[k][k] times pivot row k from every other row i over
+// the columns right of the pivot and all right-hand sides; the pivot row is
+// not normalised, so no entry a step reads is written in that step and one
+// barrier per step suffices.  At the end every row of X is divided by its
+// pivot (the pivots of an SPD matrix are the diagonal of its L D L^T
+// factorisation; "all positive and finite" is the SPD test).  The thread
+// that updates column k + 1 also publishes it as the next step's multipliers
+// in the group's tile buffer (double-buffered), so the other threads read
+// them from shared memory; without a tile buffer they read column k itself.
+// Columns are processed in register chunks of rows (all loads of a chunk
+// before its stores).  piv: M floats.  Returns false (uniformly over the
+// group) if a pivot is not positive and finite.
+template <int M, int NR, int NT>
+__device__ bool spd_solve_generic(const Grp<NT>& g, float* G, int ldg, float* X, int ldx, float* piv)
+{
+    constexpr int W = M + NR;
+    constexpr int RB = 12;
+    float* mbuf = (g.tb && 2 * M <= TileBuf::FLOATS) ? g.tb : nullptr;
+    if (mbuf) {
+        for (int i = g.t; i < M; i += NT) mbuf[i] = G[(size_t)i * ldg];
+        g.sync();
+    }
+    bool ok = true;
+    for (int k = 0; k < M; ++k) {
+        const float* mk = mbuf ? mbuf + (k & 1) * M : nullptr;
+        float* mnext = mbuf ? mbuf + ((k + 1) & 1) * M : nullptr;
+        const float pk = mk ? mk[k] : G[(size_t)k * ldg + k];
+        ok = ok && (pk > 0.f) && isfinite(pk);
+        const float ipk = 1.f / pk;
+        for (int j = k + 1 + g.t; j < W; j += NT) {
+            float* col = j < M ? G + j : X + (j - M);
+            const int ld = j < M ? ldg : ldx;
+            const float rk = col[(size_t)k * ld] * ipk;
+            const bool pub = mnext && j == k + 1 && j < M;
+            // rows in batches: every load of a batch (multipliers from the
+            // staged column when present) is issued before the batch's stores
+            for (int i0 = 0; i0 < M; i0 += RB) {
+                float mv[RB], cv[RB];
+#pragma unroll
+                for (int q = 0; q < RB; ++q) {
+                    const int i = i0 + q;
+                    const bool in = M % RB == 0 || i < M;
+                    mv[q] = in ? (mk ? mk[i] : G[(size_t)i * ldg + k]) : 0.f;
+                    cv[q] = in ? col[(size_t)i * ld] : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < RB; ++q) {
+                    const int i = i0 + q;
+                    if (M % RB == 0 || i < M) {
+                        const float v = i == k ? cv[q] : fmaf(-mv[q], rk, cv[q]);
+                        col[(size_t)i * ld] = v;   // the pivot row is stored unchanged
+                        if (pub) mnext[i] = v;
+                    }
+                }
+            }
+        }
+        if (g.t == 0) piv[k] = pk;
+        g.sync();
+    }
+    for (int e = g.t; e < M * NR; e += NT) {
+        const int i = e / NR, c = e - i * NR;
+        X[(size_t)i * ldx + c] *= 1.f / piv[i];
+    }
+    g.sync();
+    return ok;
+}
+
 // ---------------------------------------------------------------- dispatch
 // One-warp groups use the register versions (they need a small shared
 // scratch: `wsc`, at least 2 * (max(M, N) + 3) floats); wider groups use the
@@ -576,7 +839,7 @@ template <int N, int NR, int NT>
 __device__ __forceinline__ bool gj_solve(const Grp<NT>& g, float* G, int ld, float* wsc)
 {
     if constexpr (NT == 32 && N <= 32 && (N + NR + 31) / 32 <= 2) return gj_warp<N, NR>(g.t, G, ld, wsc);
-    else return gj_solve_generic<N, NR, NT>(g, G, ld);
+    else return gj_solve_generic<N, NR, NT>(g, G, ld, wsc);
 }
 
 }  // namespace pdl

@@ -102,6 +102,8 @@ template <int NX, int NU, int NT>
 struct WarpPath {
     static constexpr bool spd = NT == 32 && NU + NX + 1 <= 32;
     static constexpr bool inv = NT == 32 && 2 * NX <= 32;
+    // groups wider than one warp: SPD solves by the generic elimination
+    static constexpr bool spd_wide = NT > 32;
 };
 
 template <int NX, int NU>
@@ -179,13 +181,19 @@ __device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float
     float* Z = scr + S::Z;
     float* Y = scr + S::Y;
     constexpr int LDY = NX + 1;
-    if constexpr (WarpPath<NX, NU, NT>::spd) {
+    if constexpr (WarpPath<NX, NU, NT>::spd || WarpPath<NX, NU, NT>::spd_wide) {
         if (!has_S) {
             // [X | y] = R^-1 [B^T | r] in one elimination;  C = B X,  b = c - B y
             copy<NU, NX, true, NT, false>(g, Y, LDY, st + L::B, NU);
             for (int i = g.t; i < NU; i += NT) Y[i * LDY + NX] = st[L::r + i];
-            g.sync();
-            const bool ok = spd_solve_warp<NU, NX + 1>(g.t, st + L::R, NU, Y, LDY, Y, LDY, scr + S::Wk);
+            bool ok;
+            if constexpr (WarpPath<NX, NU, NT>::spd) {
+                g.sync();
+                ok = spd_solve_warp<NU, NX + 1>(g.t, st + L::R, NU, Y, LDY, Y, LDY, scr + S::Wk);
+            } else {
+                copy<NU, NU, false, NT>(g, Lr, NU, st + L::R, NU);
+                ok = spd_solve_generic<NU, NX + 1, NT>(g, Lr, NU, Y, LDY, dinv);
+            }
             mm<NX, NX, NU, false, false, NT, false>(g, e + E::C, NX, st + L::B, NU, Y, LDY);
             mm<NX, 1, NU, false, false, NT, false>(g, e + E::b, 1, st + L::B, NU, Y + NX, LDY,
                                                    st + L::c, 1, -1.f);
@@ -377,10 +385,13 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
     // Y2 = G^-1 [H | h];  Yr = the factor paired with Y in K^T [H | h]:
     // G^-1 [H | h] itself (SPD elimination, Y untouched) or, after a Cholesky
     // factorisation G = L L^T, Y = L^-1 [H | h] paired with itself
-    constexpr bool SPD = WarpPath<NX, NU, NT>::spd;
+    constexpr bool SPD = WarpPath<NX, NU, NT>::spd || WarpPath<NX, NU, NT>::spd_wide;
     bool ok;
-    if constexpr (SPD) {
+    if constexpr (WarpPath<NX, NU, NT>::spd) {
         ok = spd_solve_warp<NU, NX + 1>(g.t, Gm, NU, Y, LDY, Y2, LDY, scr + S::Wk);
+    } else if constexpr (WarpPath<NX, NU, NT>::spd_wide) {
+        copy<NU, NX + 1, false, NT>(g, Y2, LDY, Y, LDY);
+        ok = spd_solve_generic<NU, NX + 1, NT>(g, Gm, NU, Y2, LDY, dinv);
     } else {
         ok = chol<NU, NT>(g, Gm, NU, dinv, scr + S::Wk);
         trsm_lower<NU, NX + 1, NT>(g, Gm, NU, dinv, Y, LDY);           // [Z | z]
@@ -525,6 +536,22 @@ struct ScanSmem {
     static constexpr size_t BYTES = sizeof(float) * TOTAL;
 };
 
+// Tile buffers of the wide units (one TileBuf per unit), placed after a
+// kernel's own dynamic shared memory (base bytes) when they fit.
+template <int W, int UW>
+struct UnitTiles {
+    static constexpr size_t BYTES = UW > 1 ? (size_t)W * TileBuf::FLOATS * sizeof(float) : 0;
+    __host__ __device__ static constexpr size_t at(size_t base) { return (base + 15) & ~(size_t)15; }
+    __host__ __device__ static constexpr bool fit(size_t base)
+    {
+        return BYTES > 0 && at(base) + BYTES <= kSmemCta;
+    }
+    __host__ __device__ static constexpr size_t total(size_t base)
+    {
+        return fit(base) ? at(base) + BYTES : base;
+    }
+};
+
 // The scan solve of one instance by the CTA (all threads must call it).
 // src provides the LQ stages; s_inst points to this instance's dx_0 (global
 // or shared memory).  Returns the instance status (uniform over the CTA).
@@ -534,13 +561,14 @@ struct ScanSmem {
 // synchronised by a named barrier per unit).
 template <int NX, int NU, int W, int UW, class Src>
 __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
-                          const float* s_inst, float* smem)
+                          const float* s_inst, float* smem, float* tiles = nullptr)
 {
     using SM = ScanSmem<NX, NU, W>;
     using E = ElemL<NX>;
     constexpr int NT = 32 * UW;
     const int warp = threadIdx.x / NT;     // the unit (chunk) of this thread
-    const Grp<NT> g{(int)(threadIdx.x % NT), 1 + warp};
+    const Grp<NT> g{(int)(threadIdx.x % NT), 1 + warp,
+                    tiles ? tiles + warp * TileBuf::FLOATS : nullptr};
     const int S = N + 1;
     const int Weff = W < S ? W : S;
     const bool has_S = src.has_S();
@@ -717,12 +745,15 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     kkt_scan_kernel(const __grid_constant__ KktArgs a)
 {
     extern __shared__ __align__(16) float smem[];
+    using TL = UnitTiles<W, UW>;
     const int inst = a.order ? a.order[blockIdx.x] : blockIdx.x;
     if (inst >= a.count) return;
     const LqSource src(a);
     float* work = a.gws ? a.gws + (int64_t)blockIdx.x * ScanSmem<NX, NU, W>::TOTAL : smem;
+    const size_t base = a.gws ? 0 : ScanSmem<NX, NU, W>::BYTES;
+    float* tiles = TL::fit(base) ? smem + TL::at(base) / sizeof(float) : nullptr;
     const int st = scan_solve<NX, NU, W, UW>(src, a, a.N[inst], a.off[inst],
-                                             a.s + (int64_t)inst * NX, work);
+                                             a.s + (int64_t)inst * NX, work, tiles);
     if (threadIdx.x == 0) a.status[inst] = st;
 }
 

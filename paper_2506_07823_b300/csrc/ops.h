@@ -11,7 +11,7 @@
 
 namespace pdl {
 
-static constexpr size_t kSmemMax = 227 * 1024;  // opt-in shared memory per CTA (sm_103a)
+static constexpr size_t kSmemMax = kSmemCta;  // opt-in shared memory per CTA (sm_103a)
 
 struct SizeOps {
     int n, m;

@@ -17,23 +17,23 @@ static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
     using SM = ScanSmem<NX, NU, W>;
     if constexpr (W * UW * 32 > 1024) {
         return cudaErrorInvalidConfiguration;
-    } else if constexpr (SM::BYTES > kSmemMax) {
-        // work areas in the plan's global workspace
-        if (!a.gws) return cudaErrorInvalidConfiguration;
-        kkt_scan_kernel<NX, NU, W, UW><<<a.count, W * 32 * UW, 0, st>>>(a);
-        return cudaGetLastError();
     } else {
+        // work areas in shared memory when they fit, else in the plan's global
+        // workspace; the wide units' tile buffers after them when they fit
+        constexpr bool GWS = SM::BYTES > kSmemMax;
+        constexpr size_t bytes = UnitTiles<W, UW>::total(GWS ? 0 : SM::BYTES);
+        if (GWS && !a.gws) return cudaErrorInvalidConfiguration;
         static bool attr_set = false;
         if (!attr_set) {
             cudaError_t e = cudaFuncSetAttribute(kkt_scan_kernel<NX, NU, W, UW>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)SM::BYTES);
+                                                 (int)bytes);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
         KktArgs b = a;
-        b.gws = nullptr;          // the work areas fit in shared memory
-        kkt_scan_kernel<NX, NU, W, UW><<<a.count, W * 32 * UW, SM::BYTES, st>>>(b);
+        if (!GWS) b.gws = nullptr;
+        kkt_scan_kernel<NX, NU, W, UW><<<a.count, W * 32 * UW, bytes, st>>>(b);
         return cudaGetLastError();
     }
 }
@@ -214,7 +214,7 @@ static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
         // scan work areas in shared memory when they fit, else in the plan's
         // global workspace with the line-search extras alone in shared memory
         constexpr bool GWS = SM::SC::BYTES > kSmemMax;
-        constexpr size_t bytes = GWS ? SM::EXTRA_BYTES : SM::BYTES;
+        constexpr size_t bytes = UnitTiles<W, UW>::total(GWS ? SM::EXTRA_BYTES : SM::BYTES);
         if (GWS && !a.ka.gws) return cudaErrorInvalidConfiguration;
         static bool attr_set = false;
         if (!attr_set) {

@@ -57,7 +57,9 @@ static int pick_warps(const SizeOps* ops, int maxN)
     int w = maxN >= 40 ? 16 : (maxN >= 12 ? 8 : 4);
     while (w > 4 && (!warps_ok(ops, w) || ops->scan_smem(w) > kSmemMax)) w >>= 1;
     if (ops->scan_smem(w) > kSmemMax) {
-        w = maxN >= 40 ? 8 : 4;   // global work areas
+        // global work areas; units wider than a warp take 4 chunks, which keeps
+        // 128 registers per thread (the 1024-thread CTA of 8 such chunks spills)
+        w = (maxN >= 40 && ops->unit_warps == 1) ? 8 : 4;
         while (w > 1 && !warps_ok(ops, w)) w >>= 1;
     }
     return w;

@@ -203,9 +203,10 @@ def test_residual_kernel_matches_oracle():
         np.testing.assert_allclose(res[i], want, rtol=1e-12)
 
 
-def test_not_spd_status():
-    """A control Hessian that is not positive definite is reported, not hidden."""
-    n, m = 4, 2
+@pytest.mark.parametrize("n,m", [(4, 2), (36, 24)])
+def test_not_spd_status(n, m):
+    """A control Hessian that is not positive definite is reported, not hidden
+    (one-warp elimination at n = 4, the wide-group elimination at n = 36)."""
     insts, packed, Nv, off, s = make_batch(n, m, [6, 6], seed=9)
     packed["R"][off[1] + 2] = -np.eye(m)
     from paper_2506_07823_b300.pdilqr import Plan
