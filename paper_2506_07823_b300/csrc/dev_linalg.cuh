@@ -82,6 +82,8 @@ struct Grp {
     int t;    // rank inside the group
     int bar;  // named barrier id (groups wider than one warp)
     float* tb = nullptr;  // the group's shared-memory tile buffer (TileBuf), or none
+    float* fb = nullptr;  // the group's shared-memory factor buffer, or none
+    int fbn = 0;          // its size in floats
     __device__ __forceinline__ void sync() const {
         if constexpr (NT == 32) {
             __syncwarp();
@@ -805,6 +807,85 @@ __device__ bool spd_solve_generic(const Grp<NT>& g, float* G, int ldg, float* X,
         X[(size_t)i * ldx + c] *= 1.f / piv[i];
     }
     g.sync();
+    return ok;
+}
+
+// Floats of shared memory that spd_solve_smem needs for an M x M system:
+// the factor (rows padded to M + 1) and one block of SMEM_CB right-hand sides.
+constexpr int SMEM_CB = 64;
+__host__ __device__ constexpr int spd_smem_floats(int M) { return M * (M + 1) + M * SMEM_CB; }
+
+// G^-1 X for an SPD M x M matrix G (global or shared, read only) and NR
+// right-hand sides X (overwritten by the solution) by a group of NT threads,
+// with the factorisation resident in the group's factor buffer (at least
+// spd_smem_floats(M) floats): G is copied in and factored G = L L^T there
+// (right-looking, column by column: the pivot row scales column j, then every
+// thread updates its rows of the trailing lower triangle), and X is solved in
+// blocks of SMEM_CB columns staged beside the factor (forward substitution
+// L Y = X, then L^T Z = Y, one row of unknowns per step).  piv: M floats (the
+// reciprocal pivots).  Returns false (uniformly) if a pivot is not positive
+// and finite (G not SPD).
+template <int M, int NR, int NT>
+__device__ bool spd_solve_smem(const Grp<NT>& g, const float* G, int ldg, float* X, int ldx, float* piv)
+{
+    constexpr int LD = M + 1;   // odd row stride: threads on different rows hit different banks
+    float* L = g.fb;
+    float* Xs = g.fb + M * LD;
+    for (int e = g.t; e < M * M; e += NT) {
+        const int i = e / M, k = e - i * M;
+        L[i * LD + k] = G[(size_t)i * ldg + k];
+    }
+    g.sync();
+    bool ok = true;
+    for (int j = 0; j < M; ++j) {
+        const float d = L[j * LD + j];
+        ok = ok && (d > 0.f) && isfinite(d);
+        const float inv = rsqrtf(fmaxf(d, 1e-30f));
+        // the diagonal itself is not stored back (every thread is still
+        // reading it); the substitutions use the reciprocal pivots
+        for (int i = j + 1 + g.t; i < M; i += NT) L[i * LD + j] *= inv;
+        if (g.t == 0) piv[j] = inv;
+        g.sync();
+        // trailing update of the lower triangle, one row per thread
+        for (int i = j + 1 + g.t; i < M; i += NT) {
+            const float lij = L[i * LD + j];
+            float* Li = L + i * LD;
+            for (int k = j + 1; k <= i; ++k) Li[k] = fmaf(-lij, L[k * LD + j], Li[k]);
+        }
+        g.sync();
+    }
+    // right-hand sides: thread (rr, cc) owns column cc of rows rr, rr + RPP, ...
+    static_assert(NT % SMEM_CB == 0, "whole rows of a block per pass");
+    constexpr int RPP = NT / SMEM_CB;
+    const int cc = g.t % SMEM_CB, rr = g.t / SMEM_CB;
+    for (int c0 = 0; c0 < NR; c0 += SMEM_CB) {
+        const bool on = c0 + cc < NR;
+        for (int r = rr; r < M; r += RPP)
+            if (on) Xs[r * SMEM_CB + cc] = X[(size_t)r * ldx + c0 + cc];
+        g.sync();
+        // L Y = X: step i uses y_i = x_i / L_ii (x_i is final once the rows
+        // above have been eliminated) and removes L_ri y_i from the rows below;
+        // every row is divided by its pivot at the end
+        for (int i = 0; i < M; ++i) {
+            const float yi = piv[i] * Xs[i * SMEM_CB + cc];
+            for (int r = i + 1 + rr; r < M; r += RPP)
+                if (on) Xs[r * SMEM_CB + cc] = fmaf(-L[r * LD + i], yi, Xs[r * SMEM_CB + cc]);
+            g.sync();
+        }
+        for (int r = rr; r < M; r += RPP)
+            if (on) Xs[r * SMEM_CB + cc] *= piv[r];
+        g.sync();
+        // L^T Z = Y, from the last row up: rows above lose L_ir z_i
+        for (int i = M - 1; i > 0; --i) {
+            const float zi = piv[i] * Xs[i * SMEM_CB + cc];
+            for (int r = rr; r < i; r += RPP)
+                if (on) Xs[r * SMEM_CB + cc] = fmaf(-L[i * LD + r], zi, Xs[r * SMEM_CB + cc]);
+            g.sync();
+        }
+        for (int r = rr; r < M; r += RPP)
+            if (on) X[(size_t)r * ldx + c0 + cc] = Xs[r * SMEM_CB + cc] * piv[r];
+        g.sync();
+    }
     return ok;
 }
 

@@ -95,6 +95,10 @@ struct CombL {  // scratch of a combine
     static constexpr int SIZE = SIZE0 > SIZE1 ? SIZE0 : SIZE1;
 };
 
+// SPD systems of at least this many rows are factored in a shared-memory
+// factor buffer when the unit has one (smaller ones are eliminated in place).
+constexpr int kSmemFactorRows = 128;
+
 // One-warp fast paths: SPD solves by Gauss-Jordan without pivoting when
 // [G | H | h] fits one column per lane; the full combine through M^-1 when
 // [M | I] does.
@@ -191,8 +195,20 @@ __device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float
                 g.sync();
                 ok = spd_solve_warp<NU, NX + 1>(g.t, st + L::R, NU, Y, LDY, Y, LDY, scr + S::Wk);
             } else {
-                copy<NU, NU, false, NT>(g, Lr, NU, st + L::R, NU);
-                ok = spd_solve_generic<NU, NX + 1, NT>(g, Lr, NU, Y, LDY, dinv);
+                // large systems: the factorisation in the unit's factor buffer
+                // (compiled only where such a buffer can exist)
+                bool done = false;
+                if constexpr (NU >= kSmemFactorRows) {
+                    if (g.fb && g.fbn >= spd_smem_floats(NU)) {
+                        g.sync();
+                        ok = spd_solve_smem<NU, NX + 1, NT>(g, st + L::R, NU, Y, LDY, dinv);
+                        done = true;
+                    }
+                }
+                if (!done) {
+                    copy<NU, NU, false, NT>(g, Lr, NU, st + L::R, NU);
+                    ok = spd_solve_generic<NU, NX + 1, NT>(g, Lr, NU, Y, LDY, dinv);
+                }
             }
             mm<NX, NX, NU, false, false, NT, false>(g, e + E::C, NX, st + L::B, NU, Y, LDY);
             mm<NX, 1, NU, false, false, NT, false>(g, e + E::b, 1, st + L::B, NU, Y + NX, LDY,
@@ -391,7 +407,14 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
         ok = spd_solve_warp<NU, NX + 1>(g.t, Gm, NU, Y, LDY, Y2, LDY, scr + S::Wk);
     } else if constexpr (WarpPath<NX, NU, NT>::spd_wide) {
         copy<NU, NX + 1, false, NT>(g, Y2, LDY, Y, LDY);
-        ok = spd_solve_generic<NU, NX + 1, NT>(g, Gm, NU, Y2, LDY, dinv);
+        bool done = false;
+        if constexpr (NU >= kSmemFactorRows) {
+            if (g.fb && g.fbn >= spd_smem_floats(NU)) {
+                ok = spd_solve_smem<NU, NX + 1, NT>(g, Gm, NU, Y2, LDY, dinv);
+                done = true;
+            }
+        }
+        if (!done) ok = spd_solve_generic<NU, NX + 1, NT>(g, Gm, NU, Y2, LDY, dinv);
     } else {
         ok = chol<NU, NT>(g, Gm, NU, dinv, scr + S::Wk);
         trsm_lower<NU, NX + 1, NT>(g, Gm, NU, dinv, Y, LDY);           // [Z | z]
@@ -552,6 +575,26 @@ struct UnitTiles {
     }
 };
 
+// Factor buffers of the wide units (shared-memory SPD solves), placed after
+// the tile buffers for kernels whose work areas live in global memory, when
+// they fit.  Only for systems of 128 rows or more: smaller augmented
+// matrices stay in L1 through the elimination in place, and the buffer would
+// take that L1 away from the products.
+template <int NU, int W, int UW>
+struct UnitFactor {
+    static constexpr int FLOATS = (UW > 1 && NU >= kSmemFactorRows) ? spd_smem_floats(NU) : 0;
+    static constexpr size_t BYTES = (size_t)W * FLOATS * sizeof(float);
+    __host__ __device__ static constexpr size_t at(size_t base) { return (base + 15) & ~(size_t)15; }
+    __host__ __device__ static constexpr bool fit(size_t base)
+    {
+        return BYTES > 0 && at(base) + BYTES <= kSmemCta;
+    }
+    __host__ __device__ static constexpr size_t total(size_t base)
+    {
+        return fit(base) ? at(base) + BYTES : base;
+    }
+};
+
 // The scan solve of one instance by the CTA (all threads must call it).
 // src provides the LQ stages; s_inst points to this instance's dx_0 (global
 // or shared memory).  Returns the instance status (uniform over the CTA).
@@ -561,14 +604,17 @@ struct UnitTiles {
 // synchronised by a named barrier per unit).
 template <int NX, int NU, int W, int UW, class Src>
 __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
-                          const float* s_inst, float* smem, float* tiles = nullptr)
+                          const float* s_inst, float* smem, float* tiles = nullptr,
+                          float* factors = nullptr)
 {
     using SM = ScanSmem<NX, NU, W>;
     using E = ElemL<NX>;
     constexpr int NT = 32 * UW;
     const int warp = threadIdx.x / NT;     // the unit (chunk) of this thread
+    using UF = UnitFactor<NU, W, UW>;
     const Grp<NT> g{(int)(threadIdx.x % NT), 1 + warp,
-                    tiles ? tiles + warp * TileBuf::FLOATS : nullptr};
+                    tiles ? tiles + warp * TileBuf::FLOATS : nullptr,
+                    factors ? factors + (size_t)warp * UF::FLOATS : nullptr, factors ? UF::FLOATS : 0};
     const int S = N + 1;
     const int Weff = W < S ? W : S;
     const bool has_S = src.has_S();
@@ -750,10 +796,13 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     if (inst >= a.count) return;
     const LqSource src(a);
     float* work = a.gws ? a.gws + (int64_t)blockIdx.x * ScanSmem<NX, NU, W>::TOTAL : smem;
+    using UF = UnitFactor<NU, W, UW>;
     const size_t base = a.gws ? 0 : ScanSmem<NX, NU, W>::BYTES;
     float* tiles = TL::fit(base) ? smem + TL::at(base) / sizeof(float) : nullptr;
+    const size_t fbase = TL::total(base);
+    float* factors = (a.gws && UF::fit(fbase)) ? smem + UF::at(fbase) / sizeof(float) : nullptr;
     const int st = scan_solve<NX, NU, W, UW>(src, a, a.N[inst], a.off[inst],
-                                             a.s + (int64_t)inst * NX, work, tiles);
+                                             a.s + (int64_t)inst * NX, work, tiles, factors);
     if (threadIdx.x == 0) a.status[inst] = st;
 }
 

@@ -21,7 +21,8 @@ static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
         // work areas in shared memory when they fit, else in the plan's global
         // workspace; the wide units' tile buffers after them when they fit
         constexpr bool GWS = SM::BYTES > kSmemMax;
-        constexpr size_t bytes = UnitTiles<W, UW>::total(GWS ? 0 : SM::BYTES);
+        constexpr size_t tb = UnitTiles<W, UW>::total(GWS ? 0 : SM::BYTES);
+        constexpr size_t bytes = GWS ? UnitFactor<NU, W, UW>::total(tb) : tb;
         if (GWS && !a.gws) return cudaErrorInvalidConfiguration;
         static bool attr_set = false;
         if (!attr_set) {
@@ -214,7 +215,8 @@ static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
         // scan work areas in shared memory when they fit, else in the plan's
         // global workspace with the line-search extras alone in shared memory
         constexpr bool GWS = SM::SC::BYTES > kSmemMax;
-        constexpr size_t bytes = UnitTiles<W, UW>::total(GWS ? SM::EXTRA_BYTES : SM::BYTES);
+        constexpr size_t tb = UnitTiles<W, UW>::total(GWS ? SM::EXTRA_BYTES : SM::BYTES);
+        constexpr size_t bytes = GWS ? UnitFactor<NU, W, UW>::total(tb) : tb;
         if (GWS && !a.ka.gws) return cudaErrorInvalidConfiguration;
         static bool attr_set = false;
         if (!attr_set) {

@@ -50,8 +50,11 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     float* work = a.ka.gws ? a.ka.gws + (int64_t)blockIdx.x * SM::SC::TOTAL : smem_all;
     float* smem = a.ka.gws ? smem_all - SM::MER : smem_all;
     using TL = UnitTiles<W, UW>;
+    using UF = UnitFactor<NU, W, UW>;
     const size_t tbase = a.ka.gws ? SM::EXTRA_BYTES : SM::BYTES;
     float* tiles = TL::fit(tbase) ? smem_all + TL::at(tbase) / sizeof(float) : nullptr;
+    const size_t fbase = TL::total(tbase);
+    float* factors = (a.ka.gws && UF::fit(fbase)) ? smem_all + UF::at(fbase) / sizeof(float) : nullptr;
     const int inst = a.ka.order ? a.ka.order[blockIdx.x] : blockIdx.x;
     if (inst >= a.ka.count) return;
     const int N = a.ka.N[inst];
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     for (int it = 0; it < a.max_iters; ++it) {
         for (int i = threadIdx.x; i < NX; i += blockDim.x) sbuf[i] = xh[i] - x[i];
         __syncthreads();
-        const int st = scan_solve<NX, NU, W, UW>(src, a.ka, N, off, sbuf, work, tiles);
+        const int st = scan_solve<NX, NU, W, UW>(src, a.ka, N, off, sbuf, work, tiles, factors);
         if (st != ST_OK) {
             status = st;
             break;
