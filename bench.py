@@ -323,7 +323,13 @@ def run_gpu(args):
                 "continuous_batching_scan": measure_serving(pdilqr, args, args.serve_seconds,
                                                             args.serve_rate, 1024, 8, 2),
                 "one_request_per_launch_riccati": measure_serving(pdilqr, args, args.serve_seconds,
-                                                                  args.serve_rate, 1, 1, 1)}
+                                                                  args.serve_rate, 1, 1, 1),
+                "full_mix_workload": "Poisson arrivals, one real-time SQP iteration per request, "
+                                     "N = 50, 1024 clients: 60 % one robot, 10 % each 2, 4, 8 "
+                                     "and 16 robots (n = 12 R)",
+                "continuous_batching_full_mix": measure_serving(pdilqr, args, args.serve_seconds,
+                                                                args.serve_rate, 1024, 8, 4,
+                                                                mix="full")}
         e2e = measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args)
         cpu = None
         if pool is not None:
@@ -575,23 +581,40 @@ def measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.mean(t))}
 
 
+def client_robots(c: int, mix: str) -> int:
+    """Robots of client c: "pair" alternates one and two robots; "full" gives
+    60 % of the clients one robot and 10 % each two, four, eight and sixteen
+    (half single-robot clients, half centralised problems with R drawn
+    uniformly from {1, 2, 4, 8, 16})."""
+    if mix == "pair":
+        return 1 + (c % 2)
+    return (1, 1, 1, 1, 1, 1, 2, 4, 8, 16)[c % 10]
+
+
 def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, warps: int,
-                    inflight: int, seed: int = 0):
+                    inflight: int, seed: int = 0, mix: str = "pair"):
     """Poisson arrivals at ``rate`` requests/s for ``seconds``: each request is
-    one real-time SQP iteration of a client's MPC problem (N = 50; half the
-    clients one robot, half two robots coupled by the formation cost).
-    Returns achieved solves/s, latency percentiles and the mean batch size."""
+    one real-time SQP iteration of a client's MPC problem (N = 50; robots per
+    client as ``client_robots``, several robots coupled by the formation
+    cost).  Returns achieved solves/s, latency percentiles (overall and per
+    robot count) and the mean batch size."""
     import threading
     prm = synth.srbd_params(2)
-    srv = pdilqr.Server(prm, hbm_budget_bytes=1 << 30, max_batch=max_batch, max_inflight=inflight,
-                        max_N=50, sqp_iters=1, warps=warps)
-    n_clients = 256
-    probs = {c: synth.srbd_problem(50, seed=10_000 + c, nrob=1 + (c % 2)) for c in range(n_clients)}
+    classes = {r: synth.srbd_params(r) for r in (1, 2, 4, 8, 16)}
+    srv = pdilqr.Server(prm, hbm_budget_bytes=(1 << 30) if mix == "pair" else (16 << 30),
+                        max_batch=max_batch, max_inflight=inflight, max_N=50, sqp_iters=1,
+                        warps=warps, class_params=classes if mix != "pair" else None)
+    # a client's ticks run one after another (each warm-starts the next), so
+    # the full mix spreads the offered rate over more clients
+    n_clients = 256 if mix == "pair" else 1024
+    probs = {c: synth.srbd_problem(50, seed=10_000 + c, nrob=client_robots(c, mix))
+             for c in range(n_clients)}
     g = np.random.default_rng(seed)
     gaps = g.exponential(1.0 / rate, size=int(rate * seconds * 1.2) + 16)
     picks = g.integers(0, n_clients, size=gaps.size)
     tickets = []
     lat = []
+    lat_by = {}
     done = threading.Event()
     lock = threading.Lock()
 
@@ -609,15 +632,17 @@ def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, w
                     continue
                 time.sleep(0.0002)
                 continue
-            r = srv.poll(tk, timeout_us=60_000_000)
+            r = srv.poll(tk[0], timeout_us=60_000_000)
             lat.append(r["latency_us"])
+            lat_by.setdefault(tk[1], []).append(r["latency_us"])
             i += 1
 
     th = threading.Thread(target=collector, daemon=True)
     # admit every client once (untimed)
-    for c in range(n_clients):
-        p = probs[c]
-        srv.poll(srv.submit(c, p["nrob"], 50, p["x0hat"], p["xref"], p["uref"], p["contact"]))
+    first = [srv.submit(c, probs[c]["nrob"], 50, probs[c]["x0hat"], probs[c]["xref"],
+                        probs[c]["uref"], probs[c]["contact"]) for c in range(n_clients)]
+    for tk in first:
+        srv.poll(tk, timeout_us=60_000_000)
     th.start()
     t0 = time.perf_counter()
     t_next = t0
@@ -631,7 +656,7 @@ def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, w
         p = probs[c]
         tk = srv.submit(c, p["nrob"], 50, p["x0hat"], p["xref"], p["uref"], p["contact"])
         with lock:
-            tickets.append(tk)
+            tickets.append((tk, p["nrob"]))
         t_next += gaps[k]
         k += 1
     done.set()
@@ -639,10 +664,15 @@ def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, w
     t1 = time.perf_counter()
     st = srv.stats()
     srv.close()
-    return {"offered_per_s": rate, "requests": k, "solves_per_s": len(lat) / (t1 - t0),
-            "p50_ms": pct(lat, 50) / 1e3, "p99_ms": pct(lat, 99) / 1e3,
-            "mean_batch": st["mean_batch"], "max_batch": max_batch, "warps": warps,
-            "streams": inflight}
+    out = {"offered_per_s": rate, "requests": k, "solves_per_s": len(lat) / (t1 - t0),
+           "p50_ms": pct(lat, 50) / 1e3, "p99_ms": pct(lat, 99) / 1e3,
+           "mean_batch": st["mean_batch"], "max_batch": max_batch, "warps": warps,
+           "streams": inflight}
+    if mix != "pair":
+        out["by_robots"] = {str(r): {"requests": len(v), "p50_ms": pct(v, 50) / 1e3,
+                                     "p99_ms": pct(v, 99) / 1e3}
+                            for r, v in sorted(lat_by.items())}
+    return out
 
 
 # ------------------------------------------------------- horizon sweep

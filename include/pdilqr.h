@@ -281,8 +281,11 @@ PDILQR_API pdilqr_status pdilqr_solve(pdilqr_plan *plan, const pdilqr_srbd_model
  * PDILQR_E_ADMISSION.  All waits are bounded. */
 typedef struct {
     int64_t hbm_budget_bytes;  /* device pool for client state (0: 1 GiB)         */
-    int32_t max_batch;         /* requests per launch (0: 1024; 1: one per launch)*/
-    int32_t max_inflight;      /* batches in flight on separate streams (0: 2)    */
+    int32_t max_batch;         /* requests per launch (0: 1024; 1: one per launch);
+                                  a class of 2^c robots takes at most
+                                  max(64, max_batch / 4^c), never above max_batch */
+    int32_t max_inflight;      /* batches in flight on separate streams (0: 2);
+                                  classes of 4+ robots hold at most all but one */
     int32_t max_N;             /* longest horizon a client may use (0: 100)       */
     int32_t sqp_iters;         /* SQP iterations per request (0: 1)               */
     int32_t warps;             /* horizon chunks per instance, an upper bound    */

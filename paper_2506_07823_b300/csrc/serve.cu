@@ -276,12 +276,26 @@ void free_res(ClassRes& r)
     r = ClassRes{};
 }
 
+// Largest batch of size class cls (2^cls robots): the configured maximum for
+// one robot, a quarter of it per doubling of the robot count (the per-stage
+// workspace grows with n^2), at least 64.
+int class_batch(const pdilqr_server* sv, int cls)
+{
+    const int b = std::max(64, sv->opts.max_batch >> (2 * cls));
+    return std::min(b, sv->opts.max_batch);
+}
+
+// Classes of four or more robots run for tens of milliseconds per batch; with
+// more than one stream they may hold all but one, which stays free for the
+// one- and two-robot classes.
+constexpr int kLargeClass = 2;
+
 pdilqr_status ensure_res(pdilqr_server* sv, Slot& sl, int cls)
 {
     ClassRes& r = sl.res[cls];
     if (r.ready) return PDILQR_OK;
     const int nrob = 1 << cls, n = 12 * nrob, nc = 4 * nrob;
-    const size_t B = sv->opts.max_batch, S = B * ((size_t)sv->opts.max_N + 1);
+    const size_t B = class_batch(sv, cls), S = B * ((size_t)sv->opts.max_N + 1);
     r.n = n;
     r.nc = nc;
     // the largest warp count not above the requested one whose fused kernel
@@ -466,11 +480,19 @@ void worker_loop(pdilqr_server* sv)
         Slot* free_slot = nullptr;
         for (Slot& sl : sv->slots)
             if (!sl.busy) { free_slot = &sl; break; }
-        // the oldest request whose client is idle fixes the size class
+        // the oldest request whose client is idle fixes the size class (a large
+        // class only while it leaves a stream for the small ones)
+        int large_busy = 0;
+        for (const Slot& sl : sv->slots) large_busy += (sl.busy && sl.cls >= kLargeClass) ? 1 : 0;
+        const bool large_ok = sv->opts.max_inflight < 2 || large_busy < sv->opts.max_inflight - 1;
         int cls = -1;
         for (const Request& q : sv->pending) {
             auto c = sv->clients.find(q.client);
-            if (c != sv->clients.end() && !c->second.busy) { cls = class_of(q.nrob); break; }
+            if (c == sv->clients.end() || c->second.busy) continue;
+            const int qc = class_of(q.nrob);
+            if (qc >= kLargeClass && !large_ok) continue;
+            cls = qc;
+            break;
         }
         if (!sv->stop && free_slot && cls >= 0) {
             if (sv->opts.batch_window_us > 0 && (int)sv->pending.size() < sv->opts.max_batch) {
@@ -478,8 +500,9 @@ void worker_loop(pdilqr_server* sv)
             }
             std::vector<Request> reqs;
             std::vector<Client*> cl;
+            const int cap = class_batch(sv, cls);
             for (auto it = sv->pending.begin();
-                 it != sv->pending.end() && (int)reqs.size() < sv->opts.max_batch;) {
+                 it != sv->pending.end() && (int)reqs.size() < cap;) {
                 auto cit = sv->clients.find(it->client);
                 if (cit == sv->clients.end()) { it = sv->pending.erase(it); continue; }
                 Client& c = cit->second;
