@@ -813,7 +813,7 @@ __device__ bool spd_solve_generic(const Grp<NT>& g, float* G, int ldg, float* X,
 // Floats of shared memory that spd_solve_smem needs for an M x M system:
 // the factor (rows padded to M + 1) and one block of SMEM_CB right-hand sides.
 constexpr int SMEM_CB = 64;
-__host__ __device__ constexpr int spd_smem_floats(int M) { return M * (M + 1) + M * SMEM_CB; }
+__host__ __device__ constexpr int spd_smem_floats(int M) { return round4(M * (M + 1)) + M * SMEM_CB; }
 
 // G^-1 X for an SPD M x M matrix G (global or shared, read only) and NR
 // right-hand sides X (overwritten by the solution) by a group of NT threads,
@@ -830,60 +830,248 @@ __device__ bool spd_solve_smem(const Grp<NT>& g, const float* G, int ldg, float*
 {
     constexpr int LD = M + 1;   // odd row stride: threads on different rows hit different banks
     float* L = g.fb;
-    float* Xs = g.fb + M * LD;
+    float* Xs = g.fb + round4(M * LD);
+    // copies into the buffer go out as asynchronous copies (all in flight at
+    // once); a G already in shared memory is copied by plain loads and stores
+    const bool gsh = __isShared(G);
     for (int e = g.t; e < M * M; e += NT) {
         const int i = e / M, k = e - i * M;
-        L[i * LD + k] = G[(size_t)i * ldg + k];
+        if (gsh) L[i * LD + k] = G[(size_t)i * ldg + k];
+        else cp_async4(L + i * LD + k, G + (size_t)i * ldg + k);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     g.sync();
-    bool ok = true;
-    for (int j = 0; j < M; ++j) {
-        const float d = L[j * LD + j];
-        ok = ok && (d > 0.f) && isfinite(d);
-        const float inv = rsqrtf(fmaxf(d, 1e-30f));
-        // the diagonal itself is not stored back (every thread is still
-        // reading it); the substitutions use the reciprocal pivots
-        for (int i = j + 1 + g.t; i < M; i += NT) L[i * LD + j] *= inv;
-        if (g.t == 0) piv[j] = inv;
-        g.sync();
-        // trailing update of the lower triangle, one row per thread
-        for (int i = j + 1 + g.t; i < M; i += NT) {
-            const float lij = L[i * LD + j];
-            float* Li = L + i * LD;
-            for (int k = j + 1; k <= i; ++k) Li[k] = fmaf(-lij, L[k * LD + j], Li[k]);
+    // blocked right-looking factorisation by diagonal blocks of FB columns:
+    // one warp factors the block in registers (rows per lane), one thread per
+    // row below solves its panel row against the block's transpose (FB
+    // unknowns in registers), then the trailing lower triangle loses
+    // L21 L21^T through register tiles (thread (ty, tx): rows ty + TY q,
+    // columns 4 tx .. 4 tx + 3 of each 64-column slab)
+    constexpr int FB = M % 32 == 0 ? 32 : M % 16 == 0 ? 16 : M % 8 == 0 ? 8 : M % 4 == 0 ? 4
+                     : M % 2 == 0 ? 2 : 1;
+    // the right-hand-side area is idle during the factorisation: its first
+    // word carries the "every pivot positive" flag to all threads
+    float* okw = Xs;
+    if (g.t == 0) okw[0] = 1.f;
+    for (int jb = 0; jb < M; jb += FB) {
+        const int je = jb + FB;
+        if (g.t < 32) {
+            // Cholesky of the FB x FB diagonal block, lane i holds row i
+            const int lane = g.t;
+            float row[FB];
+#pragma unroll
+            for (int k = 0; k < FB; ++k) row[k] = lane < FB ? L[(jb + lane) * LD + jb + k] : 0.f;
+            bool okb = true;
+#pragma unroll
+            for (int j = 0; j < FB; ++j) {
+                const float d = __shfl_sync(0xffffffffu, row[j], j);
+                okb = okb && (d > 0.f) && isfinite(d);
+                const float inv = rsqrtf(fmaxf(d, 1e-30f));
+                if (lane == j) row[j] = d * inv;
+                if (lane > j) row[j] *= inv;
+                if (lane == 0) piv[jb + j] = inv;
+#pragma unroll
+                for (int k = j + 1; k < FB; ++k) {
+                    const float lkj = __shfl_sync(0xffffffffu, row[j], k);
+                    if (lane > j && k <= lane) row[k] = fmaf(-row[j], lkj, row[k]);
+                }
+            }
+            if (lane < FB) {
+#pragma unroll
+                for (int k = 0; k < FB; ++k)
+                    if (k <= lane) L[(jb + lane) * LD + jb + k] = row[k];
+            }
+            if (lane == 0 && !okb) okw[0] = 0.f;
         }
         g.sync();
+        if (je < M) {
+            // panel: row r below solves l_r L11^T = a_r (forward substitution)
+            for (int r = je + g.t; r < M; r += NT) {
+                float a[FB];
+#pragma unroll
+                for (int k = 0; k < FB; ++k) a[k] = L[r * LD + jb + k];
+#pragma unroll
+                for (int k = 0; k < FB; ++k) {
+#pragma unroll
+                    for (int l = 0; l < k; ++l) a[k] = fmaf(-a[l], L[(jb + k) * LD + jb + l], a[k]);
+                    a[k] *= piv[jb + k];
+                }
+#pragma unroll
+                for (int k = 0; k < FB; ++k) L[r * LD + jb + k] = a[k];
+            }
+            g.sync();
+            // trailing update of the lower triangle of rows/columns je..M-1
+            constexpr int TXC = 16, TYR = NT / TXC, QT = (M + TYR - 1) / TYR;
+            const int tx = g.t % TXC, ty = g.t / TXC;
+            for (int c0 = je; c0 < M; c0 += 4 * TXC) {
+                const int cb = c0 + 4 * tx;   // this thread's first column
+                float acc[QT][4];
+#pragma unroll
+                for (int q = 0; q < QT; ++q)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+                for (int k = jb; k < je; ++k) {
+                    float lc[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) lc[c] = cb + c < M ? L[(cb + c) * LD + k] : 0.f;
+#pragma unroll
+                    for (int q = 0; q < QT; ++q) {
+                        const int r = c0 + ty + TYR * q;   // rows from the slab's first column down
+                        const float lr = r < M ? L[r * LD + k] : 0.f;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(lr, lc[c], acc[q][c]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < QT; ++q) {
+                    const int r = c0 + ty + TYR * q;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (r < M && cb + c < M && cb + c <= r) L[r * LD + cb + c] -= acc[q][c];
+                }
+            }
+            g.sync();
+        }
     }
+    const bool ok = okw[0] != 0.f;
+    g.sync();   // the flag is read before the right-hand sides overwrite it
     // right-hand sides: thread (rr, cc) owns column cc of rows rr, rr + RPP, ...
     static_assert(NT % SMEM_CB == 0, "whole rows of a block per pass");
     constexpr int RPP = NT / SMEM_CB;
     const int cc = g.t % SMEM_CB, rr = g.t / SMEM_CB;
     for (int c0 = 0; c0 < NR; c0 += SMEM_CB) {
         const bool on = c0 + cc < NR;
+        const bool xsh = __isShared(X);
         for (int r = rr; r < M; r += RPP)
-            if (on) Xs[r * SMEM_CB + cc] = X[(size_t)r * ldx + c0 + cc];
+            if (on) {
+                if (xsh) Xs[r * SMEM_CB + cc] = X[(size_t)r * ldx + c0 + cc];
+                else cp_async4(Xs + r * SMEM_CB + cc, X + (size_t)r * ldx + c0 + cc);
+            }
+        cp_async_commit();
+        cp_async_wait_all();
         g.sync();
-        // L Y = X: step i uses y_i = x_i / L_ii (x_i is final once the rows
-        // above have been eliminated) and removes L_ri y_i from the rows below;
-        // every row is divided by its pivot at the end
-        for (int i = 0; i < M; ++i) {
-            const float yi = piv[i] * Xs[i * SMEM_CB + cc];
-            for (int r = i + 1 + rr; r < M; r += RPP)
-                if (on) Xs[r * SMEM_CB + cc] = fmaf(-L[r * LD + i], yi, Xs[r * SMEM_CB + cc]);
+        // L Y = X by diagonal blocks of DB rows: inside a block, step i uses
+        // y_i = x_i / L_ii and removes L_ri y_i from the block's later rows;
+        // the block's rows are then scaled to y, and every row below loses
+        // L[r][block] y[block] through a register-tiled product (thread
+        // (ty, tx): four columns, rows ty, ty + 16, ...)
+        // diagonal blocks of DB rows (the largest of 32, 16, ..., 1 dividing M)
+        constexpr int DB = M % 32 == 0 ? 32 : M % 16 == 0 ? 16 : M % 8 == 0 ? 8 : M % 4 == 0 ? 4
+                         : M % 2 == 0 ? 2 : 1;
+        const int tx = g.t % 16, ty = g.t / 16;   // 16 column groups x NT / 16 row offsets
+        constexpr int TY = NT / 16, QR = (M + TY - 1) / TY;
+        for (int kb = 0; kb < M; kb += DB) {
+            const int ke = kb + DB;
+            // the block's own triangle: one thread per column, its DB unknowns
+            // in registers (L read by broadcast), no barrier inside
+            if (g.t < SMEM_CB) {
+                float y[DB];
+#pragma unroll
+                for (int i = 0; i < DB; ++i) y[i] = Xs[(kb + i) * SMEM_CB + g.t];
+#pragma unroll
+                for (int i = 0; i < DB; ++i) {
+                    y[i] *= piv[kb + i];
+#pragma unroll
+                    for (int r = i + 1; r < DB; ++r) y[r] = fmaf(-L[(kb + r) * LD + kb + i], y[i], y[r]);
+                }
+#pragma unroll
+                for (int i = 0; i < DB; ++i) Xs[(kb + i) * SMEM_CB + g.t] = y[i];
+            }
             g.sync();
+            if (ke < M) {
+                float acc[QR][4];
+#pragma unroll
+                for (int q = 0; q < QR; ++q)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+                for (int k = kb; k < ke; ++k) {
+                    const float4 y = *reinterpret_cast<const float4*>(Xs + k * SMEM_CB + 4 * tx);
+#pragma unroll
+                    for (int q = 0; q < QR; ++q) {
+                        const int r = ke + ty + TY * q;
+                        const float l = r < M ? L[r * LD + k] : 0.f;
+                        acc[q][0] = fmaf(l, y.x, acc[q][0]);
+                        acc[q][1] = fmaf(l, y.y, acc[q][1]);
+                        acc[q][2] = fmaf(l, y.z, acc[q][2]);
+                        acc[q][3] = fmaf(l, y.w, acc[q][3]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < QR; ++q) {
+                    const int r = ke + ty + TY * q;
+                    if (r < M) {
+                        float4* px = reinterpret_cast<float4*>(Xs + r * SMEM_CB + 4 * tx);
+                        float4 v = *px;
+                        v.x -= acc[q][0]; v.y -= acc[q][1]; v.z -= acc[q][2]; v.w -= acc[q][3];
+                        *px = v;
+                    }
+                }
+                g.sync();
+            }
         }
-        for (int r = rr; r < M; r += RPP)
-            if (on) Xs[r * SMEM_CB + cc] *= piv[r];
-        g.sync();
-        // L^T Z = Y, from the last row up: rows above lose L_ir z_i
-        for (int i = M - 1; i > 0; --i) {
-            const float zi = piv[i] * Xs[i * SMEM_CB + cc];
-            for (int r = rr; r < i; r += RPP)
-                if (on) Xs[r * SMEM_CB + cc] = fmaf(-L[i * LD + r], zi, Xs[r * SMEM_CB + cc]);
+        // L^T Z = Y by the same blocks from the bottom up: rows above a block
+        // lose L[block][r]^T z[block]
+        for (int kb = M - DB; kb >= 0; kb -= DB) {
+            const int ke = kb + DB;
+            if (g.t < SMEM_CB) {
+                float z[DB];
+#pragma unroll
+                for (int i = 0; i < DB; ++i) z[i] = Xs[(kb + i) * SMEM_CB + g.t];
+#pragma unroll
+                for (int i = DB - 1; i >= 0; --i) {
+                    z[i] *= piv[kb + i];
+#pragma unroll
+                    for (int r = 0; r < i; ++r) z[r] = fmaf(-L[(kb + i) * LD + kb + r], z[i], z[r]);
+                }
+#pragma unroll
+                for (int i = 0; i < DB; ++i) Xs[(kb + i) * SMEM_CB + g.t] = z[i];
+            }
             g.sync();
+            if (kb > 0) {
+                float acc[QR][4];
+#pragma unroll
+                for (int q = 0; q < QR; ++q)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+                for (int k = kb; k < ke; ++k) {
+                    const float4 z = *reinterpret_cast<const float4*>(Xs + k * SMEM_CB + 4 * tx);
+#pragma unroll
+                    for (int q = 0; q < QR; ++q) {
+                        const int r = ty + TY * q;
+                        const float l = r < kb ? L[k * LD + r] : 0.f;
+                        acc[q][0] = fmaf(l, z.x, acc[q][0]);
+                        acc[q][1] = fmaf(l, z.y, acc[q][1]);
+                        acc[q][2] = fmaf(l, z.z, acc[q][2]);
+                        acc[q][3] = fmaf(l, z.w, acc[q][3]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < QR; ++q) {
+                    const int r = ty + TY * q;
+                    if (r < kb) {
+                        float4* px = reinterpret_cast<float4*>(Xs + r * SMEM_CB + 4 * tx);
+                        float4 v = *px;
+                        v.x -= acc[q][0]; v.y -= acc[q][1]; v.z -= acc[q][2]; v.w -= acc[q][3];
+                        *px = v;
+                    }
+                }
+                g.sync();
+            }
         }
-        for (int r = rr; r < M; r += RPP)
-            if (on) X[(size_t)r * ldx + c0 + cc] = Xs[r * SMEM_CB + cc] * piv[r];
+        for (int r0 = rr; r0 < M; r0 += 8 * RPP) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int r = r0 + q * RPP;
+                v[q] = r < M ? Xs[r * SMEM_CB + cc] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int r = r0 + q * RPP;
+                if (on && r < M) X[(size_t)r * ldx + c0 + cc] = v[q];
+            }
+        }
         g.sync();
     }
     return ok;
