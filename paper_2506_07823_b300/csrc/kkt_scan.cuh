@@ -97,7 +97,7 @@ struct CombL {  // scratch of a combine
 
 // SPD systems of at least this many rows are factored in a shared-memory
 // factor buffer when the unit has one (smaller ones are eliminated in place).
-constexpr int kSmemFactorRows = 128;
+constexpr int kSmemFactorRows = 96;
 
 // One-warp fast paths: SPD solves by Gauss-Jordan without pivoting when
 // [G | H | h] fits one column per lane; the full combine through M^-1 when
@@ -166,7 +166,7 @@ struct LqSource {
 // ------------------------------------------------------------ element build
 // e_k = (A - B R^-1 S, c - B R^-1 r, B R^-1 B^T, q - S^T R^-1 r, Q - S^T R^-1 S)
 // (Eq. initialization); the terminal element is (0, 0, 0, q_N, Q_N).
-template <int NX, int NU, int NT>
+template <int NX, int NU, int NT, bool FAC = false>
 __device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float* scr,
                               bool has_S, bool terminal)
 {
@@ -196,9 +196,9 @@ __device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float
                 ok = spd_solve_warp<NU, NX + 1>(g.t, st + L::R, NU, Y, LDY, Y, LDY, scr + S::Wk);
             } else {
                 // large systems: the factorisation in the unit's factor buffer
-                // (compiled only where such a buffer can exist)
+                // (compiled only where the launch configuration has such a buffer)
                 bool done = false;
-                if constexpr (NU >= kSmemFactorRows) {
+                if constexpr (FAC) {
                     if (g.fb && g.fbn >= spd_smem_floats(NU)) {
                         g.sync();
                         ok = spd_solve_smem<NU, NX + 1, NT>(g, st + L::R, NU, Y, LDY, dinv);
@@ -372,7 +372,7 @@ __device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, f
 // factor G = L L^T: with [Z | z] = L^-1 [H | h], K^T H = -Z^T Z and
 // K^T h = -Z^T z.  Writes P, p into vout (SMEM) and K, k, P, p,
 // Abar = A + B K, bbar = B k + c to global memory at stage gs.
-template <int NX, int NU, int NT>
+template <int NX, int NU, int NT, bool FAC = false>
 __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin, float* vout,
                              float* scr, const KktArgs& a, int64_t gs, bool has_S)
 {
@@ -408,7 +408,7 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
     } else if constexpr (WarpPath<NX, NU, NT>::spd_wide) {
         copy<NU, NX + 1, false, NT>(g, Y2, LDY, Y, LDY);
         bool done = false;
-        if constexpr (NU >= kSmemFactorRows) {
+        if constexpr (FAC) {
             if (g.fb && g.fbn >= spd_smem_floats(NU)) {
                 ok = spd_solve_smem<NU, NX + 1, NT>(g, Gm, NU, Y2, LDY, dinv);
                 done = true;
@@ -577,7 +577,7 @@ struct UnitTiles {
 
 // Factor buffers of the wide units (shared-memory SPD solves), placed after
 // the tile buffers for kernels whose work areas live in global memory, when
-// they fit.  Only for systems of 128 rows or more: smaller augmented
+// they fit.  Only for systems of 96 rows or more: smaller augmented
 // matrices stay in L1 through the elimination in place, and the buffer would
 // take that L1 away from the products.
 template <int NU, int W, int UW>
@@ -612,6 +612,9 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     constexpr int NT = 32 * UW;
     const int warp = threadIdx.x / NT;     // the unit (chunk) of this thread
     using UF = UnitFactor<NU, W, UW>;
+    // factor buffers exist for this configuration (the caller passes them
+    // whenever they fit); the shared-memory solves are compiled only then
+    constexpr bool FAC = UF::FLOATS > 0 && UF::BYTES + UnitTiles<W, UW>::BYTES + 1024 <= kSmemCta;
     const Grp<NT> g{(int)(threadIdx.x % NT), 1 + warp,
                     tiles ? tiles + warp * TileBuf::FLOATS : nullptr,
                     factors ? factors + (size_t)warp * UF::FLOATS : nullptr, factors ? UF::FLOATS : 0};
@@ -645,9 +648,9 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
             src.template load<NX, NU, NT>(g, stg, off + k, false);
             src.template keep<NX, NU, NT>(g, stg, off + k);
             if (k == k0) {
-                if (!build_element<NX, NU, NT>(g, stg, acc, scr, has_S, false)) bad = ST_NOT_SPD;
+                if (!build_element<NX, NU, NT, FAC>(g, stg, acc, scr, has_S, false)) bad = ST_NOT_SPD;
             } else {
-                if (!build_element<NX, NU, NT>(g, stg, elem, scr, has_S, false)) bad = ST_NOT_SPD;
+                if (!build_element<NX, NU, NT, FAC>(g, stg, elem, scr, has_S, false)) bad = ST_NOT_SPD;
                 if (!combine_full<NX, NT>(g, acc, elem, other, scr)) bad = ST_SINGULAR;
                 float* t = acc; acc = other; other = t;
             }
@@ -671,7 +674,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
             if (k == N) {
                 terminal_value<NX, NU, NT>(g, stg, v0, a, off + k);
             } else {
-                if (!riccati_step<NX, NU, NT>(g, stg, v0, v1, scr, a, off + k, has_S)) bad = ST_NOT_SPD;
+                if (!riccati_step<NX, NU, NT, FAC>(g, stg, v0, v1, scr, a, off + k, has_S)) bad = ST_NOT_SPD;
                 float* t = v0; v0 = v1; v1 = t;
             }
         }
@@ -728,7 +731,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         for (int k = k1 - 1; k >= k0; --k) {
             const int64_t gs = off + k;
             src.template reload<NX, NU, NT>(g, stg, gs);   // kept in phase 1
-            if (!riccati_step<NX, NU, NT>(g, stg, v0, v1, scr, a, gs, has_S)) bad = ST_NOT_SPD;
+            if (!riccati_step<NX, NU, NT, FAC>(g, stg, v0, v1, scr, a, gs, has_S)) bad = ST_NOT_SPD;
             float* t = v0; v0 = v1; v1 = t;
             __threadfence_block();
             g.sync();
