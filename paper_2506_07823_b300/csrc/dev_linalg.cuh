@@ -84,6 +84,7 @@ struct Grp {
     float* tb = nullptr;  // the group's shared-memory tile buffer (TileBuf), or none
     float* fb = nullptr;  // the group's shared-memory factor buffer, or none
     int fbn = 0;          // its size in floats
+    struct TcCtx* tc = nullptr;  // tensor-core context of the CTA (TMEM, barrier), or none
     __device__ __forceinline__ void sync() const {
         if constexpr (NT == 32) {
             __syncwarp();
@@ -118,6 +119,91 @@ struct TilePick {
 
 // Opt-in dynamic shared memory of one CTA on sm_103a.
 constexpr size_t kSmemCta = 227 * 1024;
+
+// ------------------------------------------------ tensor-core products
+// A CTA that takes products through the tensor cores owns columns of tensor
+// memory (one 128-lane fp32 accumulator of up to TMEM_TILE columns per
+// 128-row output tile) and an mbarrier on which each batch of MMAs signals
+// completion.
+constexpr int TMEM_TILE = 256;
+
+struct TcCtx {
+    uint64_t mbar;     // completion barrier of the issued MMAs
+    uint32_t tmem;     // TMEM address of the accumulators
+    uint32_t ncols;    // columns allocated (TMEM_TILE per 128-row tile)
+    uint32_t phase;    // parity the next wait expects
+    int failed;        // a wait ran out (the products written as NaN)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Allocate ncols columns (TMEM_TILE per 128-row tile of the largest
+// product; a power of two, at most 512) and set up the barrier (all threads
+// of the CTA).
+__device__ __forceinline__ void tc_setup(TcCtx* c, uint32_t ncols)
+{
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&c->tmem)), "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&c->mbar)));
+        c->ncols = ncols;
+        c->phase = 0;
+        c->failed = 0;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Release the accumulator (all threads of the CTA, after its last product).
+__device__ __forceinline__ void tc_teardown(TcCtx* c)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(c->tmem), "r"(c->ncols));
+}
+
+// Shared-memory matrix descriptor of a K-major tile without swizzle: core
+// matrices of 8 rows x 16 bytes, 128 bytes apart along K and 256 bytes
+// apart along the rows (descriptor version 1).
+__device__ __forceinline__ uint64_t tc_sdesc(const void* p)
+{
+    const uint64_t a = smem_u32(p);
+    return ((a & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) | (1ull << 46);
+}
+
+// Offset (floats) of element (r, k), k < 8, in such a tile.
+__device__ __forceinline__ int tc_koff(int r, int k) { return (r >> 3) * 64 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3); }
+
+__device__ __forceinline__ float tf32_round(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// 128-row output tiles of an R-row product, and the floats of staging the
+// product needs (high and low TF32 parts of a K-chunk of 32 of both operands).
+__host__ __device__ constexpr int tc_mtiles(int R) { return (R + 127) / 128; }
+__host__ __device__ constexpr int tc_stage_floats(int R, int C)
+{
+    return 2 * 4 * 128 * 8 * tc_mtiles(R) + 2 * 4 * C * 8;
+}
+// TMEM columns a CTA whose products have up to R rows allocates.
+__host__ __device__ constexpr int tc_cols(int R) { return tc_mtiles(R) > 1 ? 512 : TMEM_TILE; }
 
 // Tile buffer of a wide group's shared-memory tiled product: a K-chunk of
 // op(A) (BK x BM, k-major) and of op(B) (BK x BN), rows padded to LDT.
@@ -245,11 +331,168 @@ __device__ void mm_tiled(const Grp<NT>& g, float* out, int ldo, const float* A, 
 // out[R][C] = D + sgn * op(A) op(B)   (D == nullptr: no addend)
 // op(A)(r,l) = TA ? A[l*lda + r] : A[r*lda + l];  op(B)(l,c) likewise.
 // out must not alias A or B; it may alias D.
+// out[R][C] = D + sgn * op(A) op(B) on the tensor cores, for a group of 256
+// threads that is its whole CTA.  Each 128-row output tile accumulates in its
+// own TMEM columns (tile i at column TMEM_TILE i).  Per K-chunk of 32 the
+// group copies op(A) and op(B) asynchronously straight into K-major
+// positions of the factor buffer (no register round trip, all copies in
+// flight together), splits every value in place into TF32 high and low parts
+// (x = hi + lo), and one thread issues, per tile and K-step of 8, the products
+// lo(A) hi(B), hi(A) lo(B) and hi(A) hi(B) (kind::tf32, M = 128, N = C), which
+// recover FP32 accuracy (lo(A) lo(B) is below FP32 rounding).  The
+// accumulators are read back by 32x32b loads (warp w: lanes 32 (w mod 4) ..,
+// its warpgroup's 16-column slices).  Every wait is bounded; if one runs out
+// the product is written as NaN and the CTA's context marked failed.
+template <int R, int C, int K, bool TA, bool TB, int NT>
+__device__ void mm_tc(const Grp<NT>& g, float* out, int ldo, const float* A, int lda,
+                      const float* B, int ldb, const float* D, int ldd, float sgn)
+{
+    static_assert(NT == 256 && C % 32 == 0 && C <= TMEM_TILE && K % 8 == 0, "tensor-core shapes");
+    constexpr int KC = 32, MT = tc_mtiles(R), AT = 128 * 8, BT = C * 8;
+    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(C >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+    TcCtx* cx = g.tc;
+    float* Ahi = g.fb;                  // [MT][4][AT]
+    float* Alo = Ahi + MT * 4 * AT;
+    float* Bhi = Alo + MT * 4 * AT;     // [4][BT]
+    float* Blo = Bhi + 4 * BT;
+    const int t = g.t, warp = t >> 5, lane = t & 31;
+    uint32_t phase = cx->phase;
+    bool failed = cx->failed != 0;
+    const uint32_t tmem = cx->tmem;
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        const int kn = (K - k0) < KC ? (K - k0) : KC;   // multiple of 8
+        // op(A) rows 0..MT*128-1 (zero beyond R) and op(B), K-major; operands
+        // in shared memory are copied by plain loads and stores
+        const bool ash = __isShared(A), bsh = __isShared(B);
+        for (int e = t; e < MT * 128 * KC; e += NT) {
+            const int r = TA ? e % (MT * 128) : e / KC, k = TA ? e / (MT * 128) : e % KC;
+            float* d = Ahi + (r >> 7) * 4 * AT + (k >> 3) * AT + tc_koff(r & 127, k & 7);
+            if (r < R && k < kn) {
+                const float* src = TA ? A + (size_t)(k0 + k) * lda + r : A + (size_t)r * lda + k0 + k;
+                if (ash) *d = *src;
+                else cp_async4(d, src);
+            } else {
+                *d = 0.f;
+            }
+        }
+        for (int e = t; e < C * KC; e += NT) {
+            const int c = TB ? e / KC : e % C, k = TB ? e % KC : e / C;
+            float* d = Bhi + (k >> 3) * BT + tc_koff(c, k & 7);
+            if (k < kn) {
+                const float* src = TB ? B + (size_t)c * ldb + k0 + k : B + (size_t)(k0 + k) * ldb + c;
+                if (bsh) *d = *src;
+                else cp_async4(d, src);
+            } else {
+                *d = 0.f;
+            }
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        g.sync();
+        // split in place: hi stays, lo goes to the parallel buffer
+        for (int e = t; e < MT * 4 * AT; e += NT) {
+            const float x = Ahi[e], h = tf32_round(x);
+            Ahi[e] = h;
+            Alo[e] = tf32_round(x - h);
+        }
+        for (int e = t; e < 4 * BT; e += NT) {
+            const float x = Bhi[e], h = tf32_round(x);
+            Bhi[e] = h;
+            Blo[e] = tf32_round(x - h);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        g.sync();
+        if (t == 0 && !failed) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int mt = 0; mt < MT; ++mt) {
+                const uint32_t d = tmem + (uint32_t)(mt * TMEM_TILE);
+                for (int s = 0; s < kn / 8; ++s) {
+                    const float* ah = Ahi + mt * 4 * AT + s * AT;
+                    const float* al = Alo + mt * 4 * AT + s * AT;
+                    const uint32_t first = (k0 == 0 && s == 0) ? 0u : 1u;
+                    tc_mma(d, tc_sdesc(al), tc_sdesc(Bhi + s * BT), IDESC, first);
+                    tc_mma(d, tc_sdesc(ah), tc_sdesc(Blo + s * BT), IDESC, 1u);
+                    tc_mma(d, tc_sdesc(ah), tc_sdesc(Bhi + s * BT), IDESC, 1u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&cx->mbar)) : "memory");
+        }
+        if (!failed) {
+            uint32_t done = 0;
+            for (int it = 0; it < (1 << 22) && !done; ++it)
+                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                             " selp.u32 %0, 1, 0, p;\n}"
+                             : "=r"(done) : "r"(smem_u32(&cx->mbar)), "r"(phase) : "memory");
+            failed = done == 0;
+            phase ^= 1;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        g.sync();
+    }
+    // read the accumulators back: out = D + sgn * acc.  A lane holds one row
+    // of a warp's 32 x 16 slice; the slice goes through the (now idle)
+    // staging area so that the addend loads and the stores run along rows.
+    float* tb = g.fb + warp * 32 * 17;
+    for (int mt = 0; mt < MT; ++mt) {
+        const int rbase = mt * 128 + 32 * (warp & 3);
+        for (int c0 = (warp >> 2) * 16; c0 < C; c0 += 32) {
+            uint32_t v[16];
+            if (!failed) {
+                const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(mt * TMEM_TILE + c0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                             : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0x7fc00000u;   // NaN
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tb[lane * 17 + j] = __uint_as_float(v[j]);
+            __syncwarp();
+            // lane (h, c): column c0 + c of rows rbase + h, + 2, ...
+            const int c = lane & 15, h = lane >> 4;
+            float o[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int rr = h + 2 * i, gr = rbase + rr;
+                o[i] = sgn * tb[rr * 17 + c] + ((D && gr < R) ? D[(size_t)gr * ldd + c0 + c] : 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int gr = rbase + h + 2 * i;
+                if (gr < R) out[(size_t)gr * ldo + c0 + c] = o[i];
+            }
+            __syncwarp();
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    g.sync();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0) {
+        cx->phase = phase;
+        cx->failed = failed ? 1 : 0;
+    }
+}
+
 template <int R, int C, int K, bool TA, bool TB, int NT, bool SYNC = true>
 __device__ __forceinline__ void mm(const Grp<NT>& g, float* out, int ldo,
                                    const float* A, int lda, const float* B, int ldb,
                                    const float* D = nullptr, int ldd = 0, float sgn = 1.f)
 {
+    // a CTA-wide group with a tensor-core context takes large products there
+    if constexpr (NT == 256 && R >= 64 && C >= 64 && C % 32 == 0 && C <= TMEM_TILE && K >= 32 &&
+                  K % 8 == 0) {
+        if (g.tc && g.fb && g.fbn >= tc_stage_floats(R, C) && g.tc->ncols >= (uint32_t)tc_cols(R)) {
+            mm_tc<R, C, K, TA, TB, NT>(g, out, ldo, A, lda, B, ldb, D, ldd, sgn);
+            g.sync();
+            return;
+        }
+    }
     // wide groups with a tile buffer take large products through shared memory
     if constexpr ((NT == 128 || NT == 256) && R >= 48 && C >= 48 && K >= 32) {
         if (g.tb) {

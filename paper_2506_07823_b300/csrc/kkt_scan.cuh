@@ -595,6 +595,16 @@ struct UnitFactor {
     }
 };
 
+// Configurations whose products go through the tensor cores: one chunk
+// owned by a 256-thread unit (the whole CTA) with a factor buffer that can
+// stage the products.
+template <int NX, int NU, int W, int UW>
+struct UseTc {
+    static constexpr int R = NX > NU ? NX : NU;
+    static constexpr bool value = W == 1 && UW == 8 && UnitFactor<NU, W, UW>::FLOATS >= tc_stage_floats(R, R);
+    static constexpr uint32_t cols = (uint32_t)tc_cols(R);
+};
+
 // The scan solve of one instance by the CTA (all threads must call it).
 // src provides the LQ stages; s_inst points to this instance's dx_0 (global
 // or shared memory).  Returns the instance status (uniform over the CTA).
@@ -605,7 +615,7 @@ struct UnitFactor {
 template <int NX, int NU, int W, int UW, class Src>
 __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
                           const float* s_inst, float* smem, float* tiles = nullptr,
-                          float* factors = nullptr)
+                          float* factors = nullptr, TcCtx* tc = nullptr)
 {
     using SM = ScanSmem<NX, NU, W>;
     using E = ElemL<NX>;
@@ -617,7 +627,8 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     constexpr bool FAC = UF::FLOATS > 0 && UF::BYTES + UnitTiles<W, UW>::BYTES + 1024 <= kSmemCta;
     const Grp<NT> g{(int)(threadIdx.x % NT), 1 + warp,
                     tiles ? tiles + warp * TileBuf::FLOATS : nullptr,
-                    factors ? factors + (size_t)warp * UF::FLOATS : nullptr, factors ? UF::FLOATS : 0};
+                    factors ? factors + (size_t)warp * UF::FLOATS : nullptr, factors ? UF::FLOATS : 0,
+                    tc};
     const int S = N + 1;
     const int Weff = W < S ? W : S;
     const bool has_S = src.has_S();
@@ -804,8 +815,17 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     float* tiles = TL::fit(base) ? smem + TL::at(base) / sizeof(float) : nullptr;
     const size_t fbase = TL::total(base);
     float* factors = (a.gws && UF::fit(fbase)) ? smem + UF::at(fbase) / sizeof(float) : nullptr;
+    TcCtx* tc = nullptr;
+    if constexpr (UseTc<NX, NU, W, UW>::value) {
+        __shared__ TcCtx tcx;
+        if (factors) {
+            tc_setup(&tcx, UseTc<NX, NU, W, UW>::cols);
+            tc = &tcx;
+        }
+    }
     const int st = scan_solve<NX, NU, W, UW>(src, a, a.N[inst], a.off[inst],
-                                             a.s + (int64_t)inst * NX, work, tiles, factors);
+                                             a.s + (int64_t)inst * NX, work, tiles, factors, tc);
+    if (tc) tc_teardown(tc);
     if (threadIdx.x == 0) a.status[inst] = st;
 }
 

@@ -57,6 +57,16 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     float* factors = (a.ka.gws && UF::fit(fbase)) ? smem_all + UF::at(fbase) / sizeof(float) : nullptr;
     const int inst = a.ka.order ? a.ka.order[blockIdx.x] : blockIdx.x;
     if (inst >= a.ka.count) return;
+    // tensor-core products (one-chunk large states): TMEM and barrier for the
+    // whole kernel, released on its single exit path below
+    TcCtx* tc = nullptr;
+    if constexpr (UseTc<NX, NU, W, UW>::value) {
+        __shared__ TcCtx tcx;
+        if (factors) {
+            tc_setup(&tcx, UseTc<NX, NU, W, UW>::cols);
+            tc = &tcx;
+        }
+    }
     const int N = a.ka.N[inst];
     const int64_t off = a.ka.off[inst];
     const int nrob = a.md.nrob;
@@ -81,7 +91,7 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     for (int it = 0; it < a.max_iters; ++it) {
         for (int i = threadIdx.x; i < NX; i += blockDim.x) sbuf[i] = xh[i] - x[i];
         __syncthreads();
-        const int st = scan_solve<NX, NU, W, UW>(src, a.ka, N, off, sbuf, work, tiles, factors);
+        const int st = scan_solve<NX, NU, W, UW>(src, a.ka, N, off, sbuf, work, tiles, factors, tc);
         if (st != ST_OK) {
             status = st;
             break;
@@ -138,6 +148,7 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
         // direction; only the current-point column is read)
         merit_block<NX, NU>(a.md, x, u, dx, du, xr, ur, ct, xh, N, nrob, mer);
     }
+    if (tc) tc_teardown(tc);
     if (threadIdx.x == 0) {
         a.iters[inst] = iters;
         a.status[inst] = status;
