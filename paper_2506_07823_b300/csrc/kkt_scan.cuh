@@ -791,7 +791,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
 // warps for large ones.
 template <int NX>
 struct UnitWarps {
-    static constexpr int value = NX <= 24 ? 1 : (NX <= 48 ? 4 : 8);
+    static constexpr int value = NX <= 24 ? 1 : (NX <= 36 ? 4 : 8);
 };
 
 // CTAs per SM the register budget is sized for (128 registers per thread at most)
