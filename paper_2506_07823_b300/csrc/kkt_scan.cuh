@@ -111,10 +111,13 @@ struct WarpPath {
 };
 
 template <int NX, int NU>
-struct RicL {  // scratch of one Riccati step
-    static constexpr int PB = 0, PA = PB + NX * NU, w = PA + NX * NX, G = round4(w + NX),
-                         dinv = G + NU * NU, Y = round4(dinv + NU), Y2 = Y + NU * (NX + 1),
-                         Wk = round4(Y2 + NU * (NX + 1)), SIZE = round4(Wk + 3 * (NU + 1));
+struct RicL {  // scratch of one Riccati step; Y2 = G^-1 [H | h] reuses the
+               // area of P'B and P'c + p', which are dead once G and h exist
+    static constexpr int PB = 0, w = PB + NX * NU, Y2 = 0,
+                         R0 = NX * NU + NX > NU * (NX + 1) ? NX * NU + NX : NU * (NX + 1),
+                         PA = round4(R0), G = round4(PA + NX * NX), dinv = G + NU * NU,
+                         Y = round4(dinv + NU), Wk = round4(Y + NU * (NX + 1)),
+                         SIZE = round4(Wk + 3 * (NU + 1));
 };
 
 // ------------------------------------------------------------ stage loading
@@ -256,7 +259,9 @@ __device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float
 
 // ----------------------------------------------------------------- combines
 // out = e1 (x) e2 for two full elements (e1 earlier in time).  out must not
-// alias e1 or e2.
+// alias e2; it may alias e1 on the one-warp path through M^-1 (every read of
+// e1 there precedes the barrier before the first store to out, except the
+// addends P1, p1, which each thread reads at the places it then writes).
 template <int NX, int NT>
 __device__ bool combine_full(const Grp<NT>& g, const float* e1, const float* e2, float* out,
                              float* scr)
@@ -370,14 +375,14 @@ __device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, f
 // with G^-1 [H | h] from one SPD elimination without pivoting (one warp,
 // K^T [H | h] = -(G^-1 H)^T [H | h]) or, for wider systems, from the Cholesky
 // factor G = L L^T: with [Z | z] = L^-1 [H | h], K^T H = -Z^T Z and
-// K^T h = -Z^T z.  Writes P, p into vout (SMEM) and K, k, P, p,
-// Abar = A + B K, bbar = B k + c to global memory at stage gs.
+// K^T h = -Z^T z.  vin and vout hold value functions [P | p] (NX^2 + NX
+// floats).  Writes P, p into vout and K, k, P, p, Abar = A + B K,
+// bbar = B k + c to global memory at stage gs.
 template <int NX, int NU, int NT, bool FAC = false>
 __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin, float* vout,
                              float* scr, const KktArgs& a, int64_t gs, bool has_S)
 {
     using L = StageL<NX, NU>;
-    using E = ElemL<NX>;
     using S = RicL<NX, NU>;
     constexpr int LDY = NX + 1;
     float* PB = scr + S::PB;
@@ -387,8 +392,10 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
     float* dinv = scr + S::dinv;
     float* Y = scr + S::Y;
     float* Y2 = scr + S::Y2;
-    const float* P1 = vin + E::P;
-    const float* p1 = vin + E::p;
+    const float* P1 = vin;
+    const float* p1 = vin + NX * NX;
+    float* P = vout;
+    float* p = vout + NX * NX;
     mm<NX, NU, NX, false, false, NT, false>(g, PB, NU, P1, NX, st + L::B, NU);
     mm<NX, NX, NX, false, false, NT, false>(g, PA, NX, P1, NX, st + L::A, NX);
     mm<NX, 1, NX, false, false, NT, false>(g, w, 1, P1, NX, st + L::c, 1, p1, 1);
@@ -397,6 +404,9 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
     mm<NU, NX, NX, true, false, NT, false>(g, Y, LDY, st + L::B, NU, PA, NX,
                                            has_S ? st + L::S : nullptr, NX);
     mm<NU, 1, NX, true, false, NT, false>(g, Y + NX, LDY, st + L::B, NU, w, 1, st + L::r, 1);
+    // P = Q + A^T (P' A) ;  p = q + A^T w  (the K^T [H | h] terms follow)
+    mm<NX, NX, NX, true, false, NT, false>(g, P, NX, st + L::A, NX, PA, NX, st + L::Q, NX);
+    mm<NX, 1, NX, true, false, NT, false>(g, p, 1, st + L::A, NX, w, 1, st + L::q, 1);
     g.sync();
     // Y2 = G^-1 [H | h];  Yr = the factor paired with Y in K^T [H | h]:
     // G^-1 [H | h] itself (SPD elimination, Y untouched) or, after a Cholesky
@@ -422,12 +432,8 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
         trsm_lower_t<NU, NX + 1, NT>(g, Gm, NU, dinv, Y2, LDY);        // G^-1 [H | h]
     }
     const float* Yr = SPD ? Y2 : Y;
-    // P = Q + A^T (P' A) + K^T H ;  p = q + A^T w + K^T h
-    float* P = vout + E::P;
-    float* p = vout + E::p;
-    mm<NX, NX, NX, true, false, NT, false>(g, P, NX, st + L::A, NX, PA, NX, st + L::Q, NX);
-    mm<NX, 1, NX, true, false, NT, false>(g, p, 1, st + L::A, NX, w, 1, st + L::q, 1);
     g.sync();
+    // P += K^T H ;  p += K^T h
     mm<NX, NX, NU, true, false, NT, false>(g, P, NX, Y, LDY, Yr, LDY, P, NX, -1.f);
     mm<NX, 1, NU, true, false, NT, false>(g, p, 1, Y, LDY, Yr + NX, LDY, p, 1, -1.f);
     // K = -Y2[:, :NX], k = -Y2[:, NX];  Abar = A + B K;  bbar = B k + c
@@ -454,13 +460,12 @@ __device__ void terminal_value(const Grp<NT>& g, const float* st, float* vout, c
                                int64_t gs)
 {
     using L = StageL<NX, NU>;
-    using E = ElemL<NX>;
     for (int e = g.t; e < NX * NX; e += NT) {
-        vout[E::P + e] = st[L::Q + e];
+        vout[e] = st[L::Q + e];
         a.P[gs * NX * NX + e] = st[L::Q + e];
     }
     for (int i = g.t; i < NX; i += NT) {
-        vout[E::p + i] = st[L::q + i];
+        vout[NX * NX + i] = st[L::q + i];
         a.p[gs * NX + i] = st[L::q + i];
     }
     for (int e = g.t; e < NU * NX; e += NT) a.K[gs * NU * NX + e] = 0.f;
@@ -543,17 +548,28 @@ template <int NX, int NU, int W>
 struct ScanSmem {
     static constexpr int ELEM = ElemL<NX>::SIZE;
     static constexpr int STG = StageL<NX, NU>::SIZE;
-    // phase 1 (middle chunk): stage | elem | tmpE | build/combine scratch
-    static constexpr int P1 = STG + 2 * ELEM +
-                              (BuildL<NX, NU>::SIZE > CombL<NX>::SIZE ? BuildL<NX, NU>::SIZE
-                                                                      : CombL<NX>::SIZE);
-    // phase 1 (last chunk) / phase 3: stage | V0 | V1 | riccati scratch | Psi0 | Psi1 | psi
-    static constexpr int PSI = round4(2 * ELEM + STG + RicL<NX, NU>::SIZE);
-    static constexpr int P3 = PSI + 2 * NX * NX + round4(NX) * 2;
+    static constexpr int VF = round4(NX * NX + NX);   // a value function [P | p]
+    // one-warp units fold their chunk in place (the combine through M^-1 reads
+    // the earlier element completely before it overwrites it)
+    static constexpr bool INPLACE = 2 * NX <= 32;
+    // phase 1 (middle chunk): stage | build scratch, the combine's scratch
+    // over both (the stage is dead by then), then elem (| tmpE)
+    static constexpr int SB = STG + BuildL<NX, NU>::SIZE;
+    static constexpr int ELEM_AT = round4(SB > CombL<NX>::SIZE ? SB : CombL<NX>::SIZE);
+    static constexpr int P1 = ELEM_AT + (INPLACE ? 1 : 2) * ELEM;
+    // phase 2: result | combine scratch
+    static constexpr int P2 = 2 * ELEM + CombL<NX>::SIZE;
+    // phase 1 (last chunk) / phase 3: stage | V0 | V1 | riccati scratch (the
+    // chunk's closed-loop map is composed in its own slot)
+    static constexpr int P3 = STG + 2 * VF + RicL<NX, NU>::SIZE;
     static constexpr int P4 = 2 * round4(NX) + 2 * RollL<NX, NU>::SIZE;
-    static constexpr int PMAX = P1 > P3 ? P1 : P3;
-    static constexpr int PRIV = round4(PMAX > P4 ? PMAX : P4);
-    static constexpr int SLOTS = W * ELEM;
+    // a chunk slot holds its aggregate element, later its map (Psi, psi)
+    static constexpr int MAP = 2 * NX * NX + 2 * round4(NX);
+    static constexpr int SLOT = round4(ELEM > MAP ? ELEM : MAP);
+    static constexpr int PA_ = P1 > P2 ? P1 : P2;
+    static constexpr int PB_ = P3 > P4 ? P3 : P4;
+    static constexpr int PRIV = round4(PA_ > PB_ ? PA_ : PB_);
+    static constexpr int SLOTS = W * SLOT;
     static constexpr int XS = W * round4(NX);
     static constexpr int TOTAL = SLOTS + W * PRIV + XS + 4;  // + status words
     static constexpr size_t BYTES = sizeof(float) * TOTAL;
@@ -649,24 +665,26 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     // ---- phase 1
     float* stg = priv;
     if (active && !last && warp > 0) {
-        // fold e_{k0} (x) ... (x) e_{k1-1} into slots[warp]
-        float* elem = priv + SM::STG;
-        float* tmpE = elem + SM::ELEM;
-        float* scr = tmpE + SM::ELEM;
-        float* acc = slots + warp * SM::ELEM;
-        float* other = tmpE;
+        // fold e_{k0} (x) ... (x) e_{k1-1} into slots[warp]: the stage and the
+        // build scratch first, the combine scratch over both
+        static_assert(!SM::INPLACE || WarpPath<NX, NX, NT>::inv, "in-place fold needs the M^-1 combine");
+        float* bscr = priv + SM::STG;
+        float* cscr = priv;
+        float* elem = priv + SM::ELEM_AT;
+        float* acc = slots + warp * SM::SLOT;
+        float* other = SM::INPLACE ? acc : elem + SM::ELEM;
         for (int k = k0; k < k1; ++k) {
             src.template load<NX, NU, NT>(g, stg, off + k, false);
             src.template keep<NX, NU, NT>(g, stg, off + k);
             if (k == k0) {
-                if (!build_element<NX, NU, NT, FAC>(g, stg, acc, scr, has_S, false)) bad = ST_NOT_SPD;
+                if (!build_element<NX, NU, NT, FAC>(g, stg, acc, bscr, has_S, false)) bad = ST_NOT_SPD;
             } else {
-                if (!build_element<NX, NU, NT, FAC>(g, stg, elem, scr, has_S, false)) bad = ST_NOT_SPD;
-                if (!combine_full<NX, NT>(g, acc, elem, other, scr)) bad = ST_SINGULAR;
+                if (!build_element<NX, NU, NT, FAC>(g, stg, elem, bscr, has_S, false)) bad = ST_NOT_SPD;
+                if (!combine_full<NX, NT>(g, acc, elem, other, cscr)) bad = ST_SINGULAR;
                 float* t = acc; acc = other; other = t;
             }
         }
-        if (acc != slots + warp * SM::ELEM) copy<E::SIZE, 1, false, NT>(g, slots + warp * SM::ELEM, 1, acc, 1);
+        if (acc != slots + warp * SM::SLOT) copy<E::SIZE, 1, false, NT>(g, slots + warp * SM::SLOT, 1, acc, 1);
     } else if (Src::kKeeps && active && !last && warp == 0) {
         // the first chunk has no fold to do: prepare its stages for the sweep
         // (for sources that linearise on the fly this moves the work off the
@@ -678,8 +696,8 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     } else if (active && last) {
         // value-function recursion of the last chunk from the terminal cost
         float* v0 = priv + SM::STG;
-        float* v1 = v0 + SM::ELEM;
-        float* scr = v1 + SM::ELEM;
+        float* v1 = v0 + SM::VF;
+        float* scr = v1 + SM::VF;
         for (int k = k1 - 1; k >= k0; --k) {
             src.template load<NX, NU, NT>(g, stg, off + k, k == N);
             if (k == N) {
@@ -689,7 +707,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
                 float* t = v0; v0 = v1; v1 = t;
             }
         }
-        copy<E::SIZE, 1, false, NT>(g, slots + warp * SM::ELEM, 1, v0, 1);
+        copy<NX * NX + NX, 1, false, NT>(g, slots + warp * SM::SLOT + E::P, 1, v0, 1);
     }
     __syncthreads();
 
@@ -699,22 +717,22 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     {
         const int J = Weff - 1;     // items 0..J-1 live in slots 1..Weff-1
         const int j = warp - 1;
-        float* res = priv + SM::STG;             // private result buffer
+        float* res = priv;                       // private result buffer
         float* scr = res + SM::ELEM;
         for (int d = 1; d < J; d <<= 1) {
             const bool act = (j >= 0) && (j + d < J);
             bool vf = false;
             if (act) {
                 vf = (j + 2 * d - 1 >= J - 1);
-                const float* e1 = slots + (j + 1) * SM::ELEM;
-                const float* e2 = slots + (j + 1 + d) * SM::ELEM;
+                const float* e1 = slots + (j + 1) * SM::SLOT;
+                const float* e2 = slots + (j + 1 + d) * SM::SLOT;
                 const bool ok = vf ? combine_vf<NX, NT>(g, e1, e2, res, scr)
                                    : combine_full<NX, NT>(g, e1, e2, res, scr + SM::ELEM);
                 if (!ok) bad = ST_SINGULAR;
             }
             __syncthreads();
             if (act) {
-                float* dst = slots + (j + 1) * SM::ELEM;
+                float* dst = slots + (j + 1) * SM::SLOT;
                 if (vf) {
                     copy<NX * NX + NX, 1, false, NT>(g, dst + E::P, 1, res + E::P, 1);
                 } else {
@@ -727,15 +745,19 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
 
     // ---- phase 3: Riccati sweep of chunks 0..Weff-2 from their boundary
     // value functions, composing the chunk's closed-loop affine map.
-    float* psiA = priv + SM::PSI;
+    // the chunk's map (Psi, psi) is composed in its own slot once the chunk
+    // before has taken its boundary value function from there
+    float* psiA = slots + warp * SM::SLOT;
     float* psiB = psiA + NX * NX;
     float* psiv = psiB + NX * NX;
     float* psitmp = psiv + round4(NX);
+    float* v0 = priv + SM::STG;
+    float* v1 = v0 + SM::VF;
+    if (active && !last)
+        copy<NX * NX + NX, 1, false, NT, false>(g, v0, 1, slots + (warp + 1) * SM::SLOT + E::P, 1);
+    __syncthreads();
     if (active && !last) {
-        float* v0 = priv + SM::STG;
-        float* v1 = v0 + SM::ELEM;
-        float* scr = v1 + SM::ELEM;
-        copy<NX * NX + NX, 1, false, NT, false>(g, v0 + E::P, 1, slots + (warp + 1) * SM::ELEM + E::P, 1);
+        float* scr = v1 + SM::VF;
         fill<NX, NX, NT, false>(g, psiA, NX, 0.f, 1.f);
         for (int i = g.t; i < NX; i += NT) psiv[i] = 0.f;
         g.sync();
@@ -754,8 +776,8 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
             float* t2 = psiA; psiA = psiB; psiB = t2;
             g.sync();
         }
-        // publish Psi, psi at fixed slots of this warp's area
-        if (psiA != priv + SM::PSI) copy<NX * NX, 1, false, NT>(g, priv + SM::PSI, 1, psiA, 1);
+        // publish Psi, psi at the fixed place in this chunk's slot
+        if (psiA != slots + warp * SM::SLOT) copy<NX * NX, 1, false, NT>(g, slots + warp * SM::SLOT, 1, psiA, 1);
     }
     if (bad != ST_OK && g.t == 0) atomicMax(st_word, bad);
     __syncthreads();
@@ -767,7 +789,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         for (int i = g.t; i < NX; i += NT) x[i] = s_inst[i];
         g.sync();
         for (int w = 0; w + 1 < Weff; ++w) {
-            const float* Psi = smem + SM::SLOTS + w * SM::PRIV + SM::PSI;
+            const float* Psi = slots + w * SM::SLOT;
             const float* psv = Psi + 2 * NX * NX;
             mv<NX, NX, false, NT>(g, xs + (w + 1) * round4(NX), Psi, NX, xs + w * round4(NX), psv);
         }
@@ -794,14 +816,20 @@ struct UnitWarps {
     static constexpr int value = NX <= 24 ? 1 : (NX <= 36 ? 4 : 8);
 };
 
-// CTAs per SM the register budget is sized for (128 registers per thread at most)
-template <int W>
+// CTAs per SM the register budget is sized for: 16 warps per SM with up to
+// 128 registers per thread (holding these kernels to 80 registers for 24
+// warps per SM made them slower).  One-warp CTAs of the one-robot state
+// (9.2 KB of shared memory each) run 20 per SM with up to 96 registers.
+template <int NX, int WARPS>
 struct MinBlocks {
-    static constexpr int value = W >= 16 ? 1 : (W >= 8 ? 2 : (W >= 4 ? 4 : 16));
+    static constexpr int value = WARPS >= 16 ? 1
+                                 : WARPS >= 8 ? 2
+                                 : WARPS >= 4 ? 4
+                                              : (NX <= 12 ? 20 : 16);
 };
 
 template <int NX, int NU, int W, int UW>
-__global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
+__global__ void __launch_bounds__(W * 32 * UW, MinBlocks<NX, W * UW>::value)
     kkt_scan_kernel(const __grid_constant__ KktArgs a)
 {
     extern __shared__ __align__(16) float smem[];
@@ -835,7 +863,7 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
 // capacity (limit stage slots) before any access; an instance that does not
 // fit is reported as invalid and skipped.
 template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value)
+__global__ void __launch_bounds__(W * 32, MinBlocks<NX, W>::value)
     kkt_scan_checked_kernel(const __grid_constant__ KktArgs a, int64_t limit)
 {
     extern __shared__ __align__(16) float smem[];
@@ -857,7 +885,8 @@ template <int NX, int NU>
 struct RicSmem {
     static constexpr int ELEM = ElemL<NX>::SIZE;
     static constexpr int STG = StageL<NX, NU>::SIZE;
-    static constexpr int TOTAL = STG + 2 * ELEM + RicL<NX, NU>::SIZE + 2 * round4(NX) +
+    static constexpr int VF = round4(NX * NX + NX);
+    static constexpr int TOTAL = STG + 2 * VF + RicL<NX, NU>::SIZE + 2 * round4(NX) +
                                  2 * RollL<NX, NU>::SIZE;
     static constexpr size_t BYTES = sizeof(float) * TOTAL;
 };
@@ -876,8 +905,8 @@ __global__ void __launch_bounds__(128) riccati_kernel(const __grid_constant__ Kk
     float* base = smem + warp * SM::TOTAL;
     float* stg = base;
     float* v0 = base + SM::STG;
-    float* v1 = v0 + SM::ELEM;
-    float* scr = v1 + SM::ELEM;
+    float* v1 = v0 + SM::VF;
+    float* scr = v1 + SM::VF;
     float* x = scr + RicL<NX, NU>::SIZE;
     float* xn = x + round4(NX);
     float* rb = xn + round4(NX);

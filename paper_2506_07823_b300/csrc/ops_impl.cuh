@@ -7,6 +7,14 @@
 
 namespace pdl {
 
+// Dynamic shared memory of a kernel (the carveout stays the driver's choice:
+// forcing the largest one takes L1 away from the global-memory reads)
+template <class Kern>
+static cudaError_t set_smem(Kern kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 
 // W horizon chunks, each owned by UnitWarps<NX> warps; a (W, unit) pair above
 // the 1024-thread block limit is not instantiated.
@@ -26,9 +34,7 @@ static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
         if (GWS && !a.gws) return cudaErrorInvalidConfiguration;
         static bool attr_set = false;
         if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(kkt_scan_kernel<NX, NU, W, UW>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)bytes);
+            cudaError_t e = set_smem(kkt_scan_kernel<NX, NU, W, UW>, bytes);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
@@ -48,9 +54,7 @@ static cudaError_t launch_scan_checked_w(const KktArgs& a, int64_t limit, cudaSt
     } else {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kkt_scan_checked_kernel<NX, NU, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SM::BYTES);
+        cudaError_t e = set_smem(kkt_scan_checked_kernel<NX, NU, W>, SM::BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -129,9 +133,7 @@ static cudaError_t launch_riccati(const KktArgs& a, cudaStream_t st)
     } else {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(riccati_kernel<NX, NU>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)bytes);
+        cudaError_t e = set_smem(riccati_kernel<NX, NU>, bytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -183,9 +185,7 @@ static cudaError_t launch_linearize(const LinArgs& a, cudaStream_t st)
         constexpr size_t bytes = C::SPB * C::STAGE_BYTES;
         static bool attr_set = false;
         if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(linearize_kernel<NX, NU, C::SPB, C::UW>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)bytes);
+            cudaError_t e = set_smem(linearize_kernel<NX, NU, C::SPB, C::UW>, bytes);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
@@ -220,9 +220,7 @@ static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
         if (GWS && !a.ka.gws) return cudaErrorInvalidConfiguration;
         static bool attr_set = false;
         if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(sqp_kernel<NX, NU, W, UW>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)bytes);
+            cudaError_t e = set_smem(sqp_kernel<NX, NU, W, UW>, bytes);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
