@@ -257,7 +257,7 @@ def run_gpu(args):
     # --- autotune the warps per instance on this batch (one solve each)
     plans = {}
     tune = {}
-    for w in (4, 8, 16):
+    for w in ((args.warps,) if args.warps else (4, 8, 16)):
         try:
             plans[w] = pdilqr.Plan(12, 12, Nv, off, warps=w)
         except pdilqr.PdilqrError:
@@ -785,6 +785,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=COUNT)
+    ap.add_argument("--warps", type=int, default=0, choices=[0, 4, 8, 16],
+                    help="horizon chunks per instance of the batched solve (0: autotune over 4, 8, 16)")
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--comparator-sample", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")

@@ -817,19 +817,17 @@ struct UnitWarps {
 };
 
 // CTAs per SM the register budget is sized for: 16 warps per SM with up to
-// 128 registers per thread (holding these kernels to 80 registers for 24
-// warps per SM made them slower).  One-warp CTAs of the one-robot state
-// (9.2 KB of shared memory each) run 20 per SM with up to 96 registers.
-template <int NX, int WARPS>
+// 128 registers per thread.  Holding the one-robot kernels to fewer registers
+// for more warps per SM made them slower (80 registers and 24 warps: the
+// 8-chunk batch 86 ms against 72 ms; 96 registers and 20 one-warp CTAs: the
+// sequential recursion 2 % faster on the batch, 5.6 % slower on one instance).
+template <int WARPS>
 struct MinBlocks {
-    static constexpr int value = WARPS >= 16 ? 1
-                                 : WARPS >= 8 ? 2
-                                 : WARPS >= 4 ? 4
-                                              : (NX <= 12 ? 20 : 16);
+    static constexpr int value = WARPS >= 16 ? 1 : (WARPS >= 8 ? 2 : (WARPS >= 4 ? 4 : 16));
 };
 
 template <int NX, int NU, int W, int UW>
-__global__ void __launch_bounds__(W * 32 * UW, MinBlocks<NX, W * UW>::value)
+__global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     kkt_scan_kernel(const __grid_constant__ KktArgs a)
 {
     extern __shared__ __align__(16) float smem[];
@@ -863,7 +861,7 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<NX, W * UW>::value)
 // capacity (limit stage slots) before any access; an instance that does not
 // fit is reported as invalid and skipped.
 template <int NX, int NU, int W>
-__global__ void __launch_bounds__(W * 32, MinBlocks<NX, W>::value)
+__global__ void __launch_bounds__(W * 32, MinBlocks<W>::value)
     kkt_scan_checked_kernel(const __grid_constant__ KktArgs a, int64_t limit)
 {
     extern __shared__ __align__(16) float smem[];

@@ -40,7 +40,7 @@ struct SqpSmem {
 };
 
 template <int NX, int NU, int W, int UW>
-__global__ void __launch_bounds__(W * 32 * UW, MinBlocks<NX, W * UW>::value)
+__global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     sqp_kernel(const __grid_constant__ SqpArgs a)
 {
     using SM = SqpSmem<NX, NU, W>;
