@@ -112,13 +112,29 @@ struct WarpPath {
 
 template <int NX, int NU>
 struct RicL {  // scratch of one Riccati step; Y2 = G^-1 [H | h] reuses the
-               // area of P'B and P'c + p', which are dead once G and h exist
+               // area of P'B and P'c + p', which are dead once G and h exist,
+               // and Abar the area of P'A; Abar and bbar stay there for the caller
     static constexpr int PB = 0, w = PB + NX * NU, Y2 = 0,
                          R0 = NX * NU + NX > NU * (NX + 1) ? NX * NU + NX : NU * (NX + 1),
-                         PA = round4(R0), G = round4(PA + NX * NX), dinv = G + NU * NU,
+                         PA = round4(R0), Ab = PA, G = round4(PA + NX * NX), dinv = G + NU * NU,
                          Y = round4(dinv + NU), Wk = round4(Y + NU * (NX + 1)),
-                         SIZE = round4(Wk + 3 * (NU + 1));
+                         bb = round4(Wk + 3 * (NU + 1)), SIZE = round4(bb + NX);
 };
+
+// Copy COUNT floats (shared or work-area memory) to global memory, 16 bytes
+// at a time when both ends are 16-byte aligned (uniform over the group).
+template <int COUNT, int NT>
+__device__ __forceinline__ void store_out(int t, float* dst, const float* src)
+{
+    if constexpr (COUNT % 4 == 0) {
+        if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0) {
+            for (int e = t; e < COUNT / 4; e += NT)
+                reinterpret_cast<float4*>(dst)[e] = reinterpret_cast<const float4*>(src)[e];
+            return;
+        }
+    }
+    for (int e = t; e < COUNT; e += NT) dst[e] = src[e];
+}
 
 // ------------------------------------------------------------ stage loading
 // All blocks of one stage are copied asynchronously and waited for once.
@@ -376,8 +392,9 @@ __device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, f
 // K^T [H | h] = -(G^-1 H)^T [H | h]) or, for wider systems, from the Cholesky
 // factor G = L L^T: with [Z | z] = L^-1 [H | h], K^T H = -Z^T Z and
 // K^T h = -Z^T z.  vin and vout hold value functions [P | p] (NX^2 + NX
-// floats).  Writes P, p into vout and K, k, P, p, Abar = A + B K,
-// bbar = B k + c to global memory at stage gs.
+// floats).  Writes P, p into vout, Abar = A + B K and bbar = B k + c into
+// scr + RicL::Ab and scr + RicL::bb, and K, k, P, p, Abar, bbar to global
+// memory at stage gs.
 template <int NX, int NU, int NT, bool FAC = false>
 __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin, float* vout,
                              float* scr, const KktArgs& a, int64_t gs, bool has_S)
@@ -439,18 +456,25 @@ __device__ bool riccati_step(const Grp<NT>& g, const float* st, const float* vin
     // K = -Y2[:, :NX], k = -Y2[:, NX];  Abar = A + B K;  bbar = B k + c
     float* Kg = a.K + gs * NU * NX;
     float* kg = a.k + gs * NU;
-    for (int e = g.t; e < NU * NX; e += NT) Kg[e] = -Y2[(e / NX) * LDY + (e % NX)];
+    if (NX % 4 == 0 && (reinterpret_cast<uintptr_t>(Kg) & 15) == 0) {
+        for (int e = g.t; e < NU * NX / 4; e += NT) {
+            const float* y = Y2 + ((4 * e) / NX) * LDY + (4 * e) % NX;
+            reinterpret_cast<float4*>(Kg)[e] = make_float4(-y[0], -y[1], -y[2], -y[3]);
+        }
+    } else {
+        for (int e = g.t; e < NU * NX; e += NT) Kg[e] = -Y2[(e / NX) * LDY + (e % NX)];
+    }
     for (int i = g.t; i < NU; i += NT) kg[i] = -Y2[i * LDY + NX];
-    mm<NX, NX, NU, false, false, NT, false>(g, a.Abar + gs * NX * NX, NX, st + L::B, NU, Y2, LDY,
-                                            st + L::A, NX, -1.f);
-    mm<NX, 1, NU, false, false, NT, false>(g, a.bbar + gs * NX, 1, st + L::B, NU, Y2 + NX, LDY,
-                                           st + L::c, 1, -1.f);
+    float* Ab = scr + S::Ab;
+    float* bb = scr + S::bb;
+    mm<NX, NX, NU, false, false, NT, false>(g, Ab, NX, st + L::B, NU, Y2, LDY, st + L::A, NX, -1.f);
+    mm<NX, 1, NU, false, false, NT, false>(g, bb, 1, st + L::B, NU, Y2 + NX, LDY, st + L::c, 1, -1.f);
     g.sync();
     symmetrize<NX, NT>(g, P, NX);
-    float* Pg = a.P + gs * NX * NX;
-    float* pg = a.p + gs * NX;
-    for (int e = g.t; e < NX * NX; e += NT) Pg[e] = P[e];
-    for (int i = g.t; i < NX; i += NT) pg[i] = p[i];
+    store_out<NX * NX, NT>(g.t, a.P + gs * NX * NX, P);
+    store_out<NX, NT>(g.t, a.p + gs * NX, p);
+    store_out<NX * NX, NT>(g.t, a.Abar + gs * NX * NX, Ab);
+    store_out<NX, NT>(g.t, a.bbar + gs * NX, bb);
     return ok;
 }
 
@@ -769,8 +793,9 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
             __threadfence_block();
             g.sync();
             // psi <- Psi bbar_k + psi ;  Psi <- Psi Abar_k
-            mm<NX, 1, NX, false, false, NT, false>(g, psitmp, 1, psiA, NX, a.bbar + gs * NX, 1, psiv, 1);
-            mm<NX, NX, NX, false, false, NT, false>(g, psiB, NX, psiA, NX, a.Abar + gs * NX * NX, NX);
+            // (Abar_k, bbar_k as the Riccati step left them in its scratch)
+            mm<NX, 1, NX, false, false, NT, false>(g, psitmp, 1, psiA, NX, scr + RicL<NX, NU>::bb, 1, psiv, 1);
+            mm<NX, NX, NX, false, false, NT, false>(g, psiB, NX, psiA, NX, scr + RicL<NX, NU>::Ab, NX);
             g.sync();
             for (int i = g.t; i < NX; i += NT) psiv[i] = psitmp[i];
             float* t2 = psiA; psiA = psiB; psiB = t2;
