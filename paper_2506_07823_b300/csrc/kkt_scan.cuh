@@ -735,35 +735,40 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     }
     __syncthreads();
 
-    // ---- phase 2: suffix scan over chunk slots 1..Weff-1 (slot Weff-1 is a
-    // value function); slot j ends up holding the value function at the start
-    // of chunk j.
+    // ---- phase 2: suffix scan over the chunk aggregates, items 0..J-1 of
+    // chunks 1..Weff-1 (the last is a value function).  The levels alternate
+    // between two copies of the items, the chunk slots (A) and the result
+    // buffers at the start of the chunks' private areas (B), so that a level
+    // ends with one barrier; item j ends up holding the value function at the
+    // start of chunk j + 1.  Items that no longer combine are value functions
+    // and carry their P, p across.
+    const int J = Weff - 1;
+    float* const bufA = slots;                 // item i at bufA + (i + 1) SLOT
+    float* const bufB = smem + SM::SLOTS;      // item i at bufB + (i + 1) PRIV
+    bool in_b = false;                         // the copy holding the items
     {
-        const int J = Weff - 1;     // items 0..J-1 live in slots 1..Weff-1
         const int j = warp - 1;
-        float* res = priv;                       // private result buffer
-        float* scr = res + SM::ELEM;
+        float* scr = priv + SM::ELEM;          // after this chunk's own B item
         for (int d = 1; d < J; d <<= 1) {
-            const bool act = (j >= 0) && (j + d < J);
-            bool vf = false;
-            if (act) {
-                vf = (j + 2 * d - 1 >= J - 1);
-                const float* e1 = slots + (j + 1) * SM::SLOT;
-                const float* e2 = slots + (j + 1 + d) * SM::SLOT;
-                const bool ok = vf ? combine_vf<NX, NT>(g, e1, e2, res, scr)
-                                   : combine_full<NX, NT>(g, e1, e2, res, scr + SM::ELEM);
-                if (!ok) bad = ST_SINGULAR;
-            }
-            __syncthreads();
-            if (act) {
-                float* dst = slots + (j + 1) * SM::SLOT;
-                if (vf) {
-                    copy<NX * NX + NX, 1, false, NT>(g, dst + E::P, 1, res + E::P, 1);
+            const float* src = in_b ? bufB : bufA;
+            float* dst = in_b ? bufA : bufB;
+            const int ss = in_b ? SM::PRIV : SM::SLOT;
+            const int ds = in_b ? SM::SLOT : SM::PRIV;
+            if (j >= 0 && j < J) {
+                const float* e1 = src + (j + 1) * ss;
+                float* out = dst + (j + 1) * ds;
+                if (j + d < J) {
+                    const bool vf = (j + 2 * d - 1 >= J - 1);
+                    const float* e2 = src + (j + 1 + d) * ss;
+                    const bool ok = vf ? combine_vf<NX, NT>(g, e1, e2, out, scr)
+                                       : combine_full<NX, NT>(g, e1, e2, out, scr + SM::ELEM);
+                    if (!ok) bad = ST_SINGULAR;
                 } else {
-                    copy<E::SIZE, 1, false, NT>(g, dst, 1, res, 1);
+                    copy<NX * NX + NX, 1, false, NT>(g, out + E::P, 1, e1 + E::P, 1);
                 }
             }
             __syncthreads();
+            in_b = !in_b;
         }
     }
 
@@ -777,8 +782,10 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     float* psitmp = psiv + round4(NX);
     float* v0 = priv + SM::STG;
     float* v1 = v0 + SM::VF;
-    if (active && !last)
-        copy<NX * NX + NX, 1, false, NT, false>(g, v0, 1, slots + (warp + 1) * SM::SLOT + E::P, 1);
+    if (active && !last) {
+        const float* vb = in_b ? bufB + (warp + 1) * SM::PRIV : bufA + (warp + 1) * SM::SLOT;
+        copy<NX * NX + NX, 1, false, NT, false>(g, v0, 1, vb + E::P, 1);
+    }
     __syncthreads();
     if (active && !last) {
         float* scr = v1 + SM::VF;
