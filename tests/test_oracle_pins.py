@@ -306,6 +306,67 @@ def test_barrier_golden_and_c2():
         assert abs((vp[1] - vm[1]) / (2 * h) - v[2]) < 1e-6
 
 
+# ------------------------------------------- SRBD cost and merit assembly
+SRBD_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "srbd_cost_merit.json")
+
+
+def _golden_params(gold, case):
+    """Model constants of a golden case: its own, or another case's with overrides."""
+    c = gold[case]
+    base = dict(gold[c.get("params_from", case)]["params"])
+    base.update(c.get("overrides", {}))
+    return {k: (np.asarray(v, dtype=np.float64) if isinstance(v, list) else v)
+            for k, v in base.items()}
+
+
+def test_srbd_stage_cost_golden():
+    """Stage and terminal cost of one robot against hand arithmetic: tracking,
+    control, the five pyramid rows of two stance feet on both barrier
+    branches, and a swing foot that contributes no barrier."""
+    gold = json.load(open(SRBD_GOLDEN))
+    c = gold["stage_cost_one_robot"]
+    p = _golden_params(gold, "stage_cost_one_robot")
+    ct = np.asarray(c["contact"], dtype=np.uint8)
+    J = oracle.srbd_cost(p, c["x"], c["u"], ct, c["xref"], c["uref"], False)
+    assert J == pytest.approx(c["stage"], rel=1e-13, abs=1e-15)
+    Jt = oracle.srbd_cost(p, c["x"], None, None, c["xref"], None, True)
+    assert Jt == pytest.approx(c["terminal"], rel=1e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("case", ["formation_two_robots", "formation_four_robots"])
+def test_srbd_formation_cost_golden(case):
+    """Ring formation term against hand arithmetic (sign and owner of each
+    offset d_a, wrap-around of the ring)."""
+    gold = json.load(open(SRBD_GOLDEN))
+    c = gold[case]
+    p = _golden_params(gold, case)
+    R = p["nrob"]
+    x = np.zeros(12 * R)
+    for a, pos in enumerate(c["positions"]):
+        x[12 * a:12 * a + 3] = pos
+    u = np.zeros(12 * R)
+    ct = np.zeros(4 * R, dtype=np.uint8)
+    J = oracle.srbd_cost(p, x, u, ct, x, u, False)
+    assert J == pytest.approx(c["stage"], rel=1e-13, abs=1e-15)
+    Jt = oracle.srbd_cost(p, x, None, None, x, None, True)
+    assert Jt == pytest.approx(c["terminal"], rel=1e-13, abs=1e-15)
+
+
+def test_srbd_merit_golden():
+    """J and theta of a two-interval trajectory against hand arithmetic,
+    including the initial-state term |xhat_0 - x_0|."""
+    gold = json.load(open(SRBD_GOLDEN))
+    c = gold["merit_free_fall"]
+    p = _golden_params(gold, "merit_free_fall")
+    N = c["N"]
+    x = np.asarray(c["x"], dtype=np.float64)
+    zeros = np.zeros((N + 1, 12))
+    ct = np.zeros((N + 1, 4), dtype=np.uint8)
+    J, th = oracle.srbd_merit(p, np.asarray(c["x0hat"]), x, zeros, zeros, zeros, ct)
+    assert J == pytest.approx(c["J"], rel=1e-13)
+    assert th == pytest.approx(c["theta"], rel=1e-13)
+
+
 # -------------------------------------------------------------- SRBD model
 def test_srbd_free_fall_and_torque():
     p = synth.srbd_params()
