@@ -51,16 +51,52 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sqp_kernel_traffic.json")
 KERNEL_SOURCES = ["dev_linalg.cuh", "kkt_scan.cuh", "srbd.cuh", "sqp.cuh"]
 
-# FP32 FMA peak of a B300 from its unit counts: 148 SMs x 128 FP32 lanes x
-# 2 flop x 2.032 GHz (maximum SM clock).
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+def flops_per_stage(n: int, solver: str) -> float:
+    """Algorithmic flops of one LQ KKT solve per stage for n = m: about 50 n^3
+    for the work-efficient scan (combines in both sweeps, element build,
+    policy, trajectory) and about 13 n^3 for the sequential Riccati recursion
+    (4 n^3 + 8 n^2 m + m^3 / 3)."""
+    return (50.0 if solver == "scan" else 13.0) * n ** 3
 
 
-def flops_per_stage(n: int) -> float:
-    """Algorithmic flops of one LQ KKT solve per stage for n = m, the
-    work-efficient scan (combines in both sweeps, element build, policy,
-    trajectory): about 50 n^3."""
-    return 50.0 * n ** 3
+def _gj_flops(rows: int, cols: int) -> float:
+    """Gauss-Jordan elimination of a rows x (rows + cols) augmented matrix as
+    the kernels run it: every step updates the rows - 1 other rows over the
+    columns right of the pivot (2 flop each), then the right-hand sides are
+    divided by the pivots."""
+    return sum(2.0 * (rows - 1) * (rows + cols - k - 1) for k in range(rows)) + rows * cols
+
+
+def executed_flops(n: int, m: int, N: int, chunks: int) -> float:
+    """Flops the LQ KKT solve of one instance executes in the fused kernel,
+    counted from the operation sizes of the code: a Riccati step per stage
+    (P'B, P'A, P'c, G, H, h, A^T P'A, A^T w, the SPD elimination of
+    G^-1 [H | h], K^T H, K^T h, Abar, bbar), and for a scan with W > 2 chunks
+    per stage of the middle chunks an element build (R^-1 [B^T | r], B X, b)
+    and a full combine (C1 P2, P2 A1, the inversion of M = I + C1 P2, M^-1 A1,
+    M^-1 C1, the five output blocks), per stage of every chunk but the last
+    the chunk-map update (Psi Abar, Psi bbar), and per stage the rollout.
+    The chunk partition is the kernels' (every chunk one stage, the rest in
+    proportion 10 : 16 for the first/middle and the last chunk)."""
+    ric = (2 * n * n * m + 2 * n ** 3 + 2 * n * n + 2 * m * m * n + 2 * m * n * n + 2 * m * n
+           + 2 * n ** 3 + 2 * n * n + _gj_flops(m, n + 1) + 2 * n * n * m + 2 * n * m
+           + 2 * n * n * m + 2 * n * m)
+    build = _gj_flops(m, n + 1) + 2 * n * n * m + 2 * n * m
+    comb = 16 * n ** 3 + 6 * n * n + _gj_flops(n, n)
+    cmap = 2 * n ** 3 + 2 * n * n
+    roll = 4 * n * n + 2 * n * m
+    S = N + 1
+    W = min(chunks, S)
+    per = S * (ric + roll)
+    if W > 1:
+        units = (W - 1) * 10 + 16
+        start = [w + ((S - W) * (w * 10)) // units for w in range(W)] + [S]
+        for w in range(W - 1):
+            size = start[w + 1] - start[w]
+            per += size * cmap
+            if w > 0:
+                per += size * (build + comb)
+    return per
 
 
 def kernel_source_hash() -> str:
@@ -74,27 +110,72 @@ def kernel_source_hash() -> str:
 # --------------------------------------------------------------- CPU oracle
 def _oracle_worker(args):
     import oracle  # test infrastructure: only the CPU-baseline leg runs it
-    prm, items = args
-    its = 0
-    for pr in items:
-        _, _, _, info = oracle.srbd_sqp(prm, pr["x0hat"], pr["x"], pr["u"], pr["lam"],
-                                        pr["xref"], pr["uref"], pr["contact"], max_iters=ITERS)
+    prm, items, keep = args
+    its, kept = 0, []
+    for idx, pr in items:
+        x, u, lam, info = oracle.srbd_sqp(prm, pr["x0hat"], pr["x"], pr["u"], pr["lam"],
+                                          pr["xref"], pr["uref"], pr["contact"], max_iters=ITERS)
         its += info["iters"]
-    return its
+        if keep:
+            kept.append((idx, x, u, lam, int(info["status"]), np.asarray(info["alpha"][:ITERS])))
+    return its, kept
 
 
 def oracle_pool(cores: int):
     return mp.get_context("spawn").Pool(cores)
 
 
-def oracle_run(pool, cores: int, insts: list) -> tuple[int, float]:
+def oracle_run(pool, cores: int, insts: list, keep: bool = False):
     """Solve ``insts`` with the FP64 oracle on ``cores`` processes; returns
-    (KKT solves, wall seconds)."""
+    (KKT solves, wall seconds, per-instance results if ``keep``).  The oracle
+    gets the FP32-rounded problem data, as the GPU does."""
     prm = synth.srbd_params()
-    chunks = [insts[i::cores] for i in range(cores)]
+    items = [(i, {**{k: np.asarray(pr[k], np.float32).astype(np.float64)
+                     for k in ("x0hat", "x", "u", "lam", "xref", "uref")},
+                  "contact": pr["contact"]}) for i, pr in enumerate(insts)]
+    chunks = [items[i::cores] for i in range(cores)]
     t0 = time.perf_counter()
-    its = sum(pool.map(_oracle_worker, [(prm, c) for c in chunks if c]))
-    return its, time.perf_counter() - t0
+    res = pool.map(_oracle_worker, [(prm, c, keep) for c in chunks if c])
+    secs = time.perf_counter() - t0
+    its = sum(r[0] for r in res)
+    kept = sorted((k for r in res for k in r[1]), key=lambda t: t[0])
+    return its, secs, kept
+
+
+def compare_with_oracle(kept, Nv, off, x, u, lam, status, alpha) -> dict:
+    """Final iterates of the timed batch against the oracle's free-running
+    solves of the same instances: status agreement, and per block
+    |z_gpu - z_ref|_inf / |z_ref|_inf over the instances both end with status
+    OK (all of them, and those whose step sizes agree at every iteration, where
+    the two runs take the same path and must agree to 1e-4)."""
+    agree = {}
+    err_all = {"x": [], "u": [], "lam": []}
+    err_same = {"x": [], "u": [], "lam": []}
+    for idx, xr, ur, lr, st_o, al_o in kept:
+        st_g = int(status[idx])
+        key = f"gpu{st_g}_oracle{st_o}"
+        agree[key] = agree.get(key, 0) + 1
+        if st_g != 0 or st_o != 0:
+            continue
+        N, o = int(Nv[idx]), int(off[idx])
+        e = {"x": np.abs(x[o:o + N + 1] - xr).max() / max(np.abs(xr).max(), 1e-30),
+             "u": np.abs(u[o:o + N] - ur[:N]).max() / max(np.abs(ur[:N]).max(), 1e-30),
+             "lam": np.abs(lam[o:o + N + 1] - lr).max() / max(np.abs(lr).max(), 1e-30)}
+        same = np.array_equal(alpha[idx].astype(np.float64), al_o)
+        for k in e:
+            err_all[k].append(e[k])
+            if same:
+                err_same[k].append(e[k])
+    out = {"instances_compared": len(kept), "status_agreement": dict(sorted(agree.items())),
+           "ok_pairs": len(err_all["x"]), "ok_pairs_same_steps": len(err_same["x"])}
+    for name, errs in (("all_ok_pairs", err_all), ("same_steps", err_same)):
+        if errs["x"]:
+            out[name] = {
+                "max_rel_err": {k: float(np.max(v)) for k, v in errs.items()},
+                "p99_rel_err": {k: float(np.percentile(v, 99)) for k, v in errs.items()},
+                "within_1e-4": int(sum(max(errs[k][i] for k in errs) <= 1e-4
+                                       for i in range(len(errs["x"]))))}
+    return out
 
 
 def host_cores() -> int:
@@ -254,10 +335,14 @@ def run_gpu(args):
     def flush():
         flush_buf.zero_()
 
-    # --- autotune the warps per instance on this batch (one solve each)
+    # measured FP32 FMA peak of this GPU (the roofline's denominator)
+    peak_ffma, _ = pdilqr.peak_probe(pdilqr.PEAK_FFMA, 3)
+
+    # --- autotune the solver on this batch: the sequential recursion (one
+    # chunk per instance) and the scan with 4, 8 or 16 chunks; one solve each
     plans = {}
     tune = {}
-    for w in ((args.warps,) if args.warps else (4, 8, 16)):
+    for w in ((args.warps,) if args.warps else (1, 4, 8, 16)):
         try:
             plans[w] = pdilqr.Plan(12, 12, Nv, off, warps=w)
         except pdilqr.PdilqrError:
@@ -271,9 +356,11 @@ def run_gpu(args):
         tune[w] = min(event_times(torch, solve_w, 2, stream, before=lambda: (reset(), flush())))
     W = min(tune, key=tune.get)
     plan = plans[W]
+    solver = "sequential" if W == 1 else "scan"
     info = {"iters": torch.zeros(plan.count, device=dev, dtype=torch.int32),
             "status": torch.zeros(plan.count, device=dev, dtype=torch.int32),
-            "alpha": None, "J": None, "theta": None}
+            "alpha": torch.zeros(plan.count, ITERS, device=dev, dtype=torch.float32),
+            "J": None, "theta": None}
 
     def solve_direct():
         plan.solve(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"],
@@ -309,21 +396,26 @@ def run_gpu(args):
     clk = clocks.stop()
     kkt_per_step = int(info["iters"].sum().item())
     st = info["status"].cpu().numpy()
+    final = {k: work[k].double().cpu().numpy() for k in ("x", "u", "lam")}
+    alpha_gpu = info["alpha"].cpu().numpy()
     ms, kkt_all = aggregate(float(np.mean(times)), float(kkt_per_step), dev)
     value = kkt_all / (ms / 1e3)
 
     result = None
     if rank == 0:
         n = 12
-        achieved = flops_per_stage(n) * total_stages * (kkt_per_step / plan.count) / (ms / 1e3) / 1e12
+        its_inst = info["iters"].cpu().numpy()
+        algo = flops_per_stage(n, solver) * float(np.sum((Nv + 1) * its_inst))
+        executed = sum(executed_flops(n, n, int(Nv[i]), W) * int(its_inst[i]) for i in range(len(Nv)))
+        achieved = algo / (ms / 1e3) / 1e12
         traffic = None
         try:
-            tr = json.load(open(TRAFFIC_FILE))
+            tr = json.load(open(TRAFFIC_FILE)).get(f"sqp_kernel<12,12,{W},1>", {})
             if tr.get("source_hash") == kernel_source_hash():
                 traffic = tr["bytes_per_launch_full"]
         except Exception:
             traffic = None
-        extras = measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args)
+        extras = measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, plans, args)
         lqw = measure_lq_workloads(torch, pdilqr, dev, stream, args) if args.lq_workloads else None
         serving = None
         if args.serve_seconds > 0:
@@ -342,12 +434,15 @@ def run_gpu(args):
                                                                 mix="full")}
         e2e = measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args)
         cpu = None
+        vs_oracle = None
         if pool is not None:
             sample = insts[:sample_size(cores)]
-            its, secs = oracle_run(pool, cores, sample)
+            its, secs, kept = oracle_run(pool, cores, sample, keep=True)
             cpu = {"value": its / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"{len(sample)} of the {args.count} instances, one 10-iteration "
                              f"SQP solve each, FP64 C oracle, {cores} processes, {secs:.1f} s"}
+            vs_oracle = compare_with_oracle(kept, Nv, off, final["x"], final["u"], final["lam"],
+                                            st, alpha_gpu)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -356,6 +451,8 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "instances_per_gpu": args.count,
                        "horizons": list(HORIZONS), "n": 12, "m": 12, "sqp_iters": ITERS,
                        "stages_per_gpu": total_stages, "warps_per_instance": W,
+                       "solver": ("sequential Riccati recursion (one chunk per instance)"
+                                  if W == 1 else f"parallel scan ({W} horizon chunks)"),
                        "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()},
                        "l2": "flushed between timed steps (256 MiB write)",
                        "cuda_graph": "the timed step replays a captured graph of the batched solve",
@@ -366,12 +463,18 @@ def run_gpu(args):
             "serving": serving,
             "lq_workloads": lqw,
             "status_counts": {str(int(s)): int((st == s).sum()) for s in np.unique(st)},
+            "vs_oracle": vs_oracle,
             "kkt_solves_per_step": kkt_all,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ffma,
+                         "unit": "TFLOP/s", "frac": achieved / peak_ffma,
                          "traffic": traffic,
-                         "kernel": f"sqp_kernel<12,12,{W}>",
-                         "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 x 2.032 GHz"},
+                         "kernel": f"sqp_kernel<12,12,{W},1>",
+                         "algorithmic_flops_per_step": algo,
+                         "algorithmic_flops_per_stage": flops_per_stage(n, solver),
+                         "executed_kkt_flops_per_step": executed,
+                         "executed_frac": executed / (ms / 1e3) / 1e12 / peak_ffma,
+                         "peak_source": "measured in this run: FFMA probe (pdilqr_peak_probe), "
+                                        "best of 3 launches of about 50 ms"},
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -386,7 +489,7 @@ def run_gpu(args):
     return result
 
 
-def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args):
+def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, plans, args):
     """Single-instance latencies (MPC tick) and the comparators."""
     lat, comp = {}, {}
     # one N = 50 problem, the paper's SRBD MPC tick
@@ -416,30 +519,40 @@ def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, args):
         t = event_times(torch, g.replay, reps, stream)
         lat[name + "_p50"] = pct(t, 50)
         lat[name + "_p99"] = pct(t, 99)
-    # the same batch through the sequential recursion: the fused SQP with one
-    # horizon chunk per instance (one warp, 16 CTAs per SM)
-    p1 = pdilqr.Plan(12, 12, plan.N, plan.stage_off, warps=1)
-    inf1 = {"iters": torch.zeros(p1.count, device=dev, dtype=torch.int32),
-            "status": torch.zeros(p1.count, device=dev, dtype=torch.int32),
-            "alpha": None, "J": None, "theta": None}
-
-    def ric_batch():
-        p1.solve(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"], work["uref"],
-                 work["contact"], max_iters=ITERS, info=inf1)
-
+    # the same batch through every solver of the autotuner: the sequential
+    # recursion (the fused SQP with one horizon chunk per instance, one warp,
+    # 16 CTAs per SM) and the scan with 4, 8, 16 chunks
     def reset_work():
         for k in ("x", "u", "lam"):
             work[k].copy_(base[k], non_blocking=True)
-    reset_work()
-    ric_batch()
-    torch.cuda.synchronize()
-    t = event_times(torch, ric_batch, 3, stream, before=reset_work)
-    comp["riccati_sqp_batched"] = {
-        "kkt_solves_per_s": float(inf1["iters"].sum().item()) / (np.mean(t) / 1e3),
-        "ms": float(np.mean(t)), "warps_per_instance": 1,
-        "note": "same 4096-instance batch and fused SQP kernel, one horizon chunk per instance "
-                "(the sequential Riccati recursion)"}
-    p1.close()
+
+    by_chunks = {}
+    for w in sorted(plans):
+        pw = plans[w]
+        infw = {"iters": torch.zeros(pw.count, device=dev, dtype=torch.int32),
+                "status": torch.zeros(pw.count, device=dev, dtype=torch.int32),
+                "alpha": None, "J": None, "theta": None}
+
+        def batch(pw=pw, infw=infw):
+            pw.solve(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"],
+                     work["uref"], work["contact"], max_iters=ITERS, info=infw)
+        reset_work()
+        batch()
+        torch.cuda.synchronize()
+        t = event_times(torch, batch, 3, stream, before=reset_work)
+        by_chunks[w] = {"kkt_solves_per_s": float(infw["iters"].sum().item()) / (np.mean(t) / 1e3),
+                        "ms": float(np.mean(t))}
+    if 1 in by_chunks:
+        comp["riccati_sqp_batched"] = dict(
+            by_chunks[1], warps_per_instance=1,
+            note="same batch and fused SQP kernel, one horizon chunk per instance (the "
+                 "sequential Riccati recursion)")
+    scans = {w: v for w, v in by_chunks.items() if w > 1}
+    if scans:
+        wb = min(scans, key=lambda w: scans[w]["ms"])
+        comp["scan_sqp_batched"] = dict(scans[wb], warps_per_instance=wb,
+                                        note="same batch, the parallel scan at its best chunk count")
+    comp["sqp_batched_by_chunks"] = {str(w): v for w, v in by_chunks.items()}
     # LQ KKT solves alone on the linearisation of the 4096-instance batch
     lq = plan.linearize(md, base)
     lq["S"] = None
@@ -523,14 +636,15 @@ def measure_lq_workloads(torch, pdilqr, dev, stream, args):
         bwd = pdilqr.backward_error(o["resid"]).cpu().numpy()
         errs = []
         dx = o["dx"].double().cpu().numpy()
-        for i in range(0, len(allinst), len(allinst) // 4):
+        for i in range(0, uniq, uniq // 8):     # eight distinct instances
             N, o0 = int(Nv[i]), int(off[i])
             r32 = {k: np.asarray(allinst[i][k], np.float32).astype(np.float64) for k in synth.LQ_KEYS}
             ref = oracle.riccati_solve(r32, np.asarray(s[i], np.float32).astype(np.float64))
             errs.append(float(np.abs(dx[o0:o0 + N + 1] - ref["dx"]).max() / np.abs(ref["dx"]).max()))
         wb[name] = {"kkt_solves_per_s": len(allinst) / (np.mean(t) / 1e3), "ms": float(np.mean(t)),
                     "warps": plan.warps, "max_backward_error": float(bwd.max()),
-                    "max_rel_error_vs_oracle_sample": max(errs)}
+                    "max_rel_error_vs_oracle_sample": max(errs),
+                    "oracle_sample": "8 distinct instances (0, 16, ..., 112 of the 128)"}
         plan.close()
     out["whole_body_lq_batch"] = wb
     # single LQR (n = 4, m = 2, N = 16), graph replays
@@ -744,6 +858,28 @@ def run_sweep(args):
             "work_ratio_scan_to_riccati": "about 50 n^3 vs 13 n^3 flop per stage (n = m)"}
 
 
+# ------------------------------------------------------------ peak probes
+def run_peaks(args):
+    """Measured peak rates of this GPU's FP32 and FP64 FMA pipes and of its
+    tensor cores on TF32 (tcgen05.mma, M = 128, N = 256, K = 8), best of five
+    launches of about 50 ms each, with the SM clocks sampled meanwhile."""
+    import torch
+    from paper_2506_07823_b300 import pdilqr
+    torch.cuda.set_device(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    out = {}
+    for name, kind in (("ffma_tflops", pdilqr.PEAK_FFMA), ("dfma_tflops", pdilqr.PEAK_DFMA),
+                       ("tf32_mma_tflops", pdilqr.PEAK_TF32_MMA)):
+        tf, ms = pdilqr.peak_probe(kind, 5)
+        out[name] = tf
+        out[name.replace("tflops", "launch_ms")] = ms
+    out["clocks"] = clocks.stop()
+    out["gpu"] = torch.cuda.get_device_name(0)
+    out["sms"] = torch.cuda.get_device_properties(0).multi_processor_count
+    return out
+
+
 # --------------------------------------------------------- reference arm
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -758,7 +894,7 @@ def run_reference(args):
         oracle_run(pool, cores, sample[:cores])
     tot_its, tot_s, per = 0, 0.0, []
     for _ in range(args.steps):
-        its, secs = oracle_run(pool, cores, sample)
+        its, secs, _ = oracle_run(pool, cores, sample)
         tot_its += its
         tot_s += secs
         per.append(secs)
@@ -785,8 +921,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=COUNT)
-    ap.add_argument("--warps", type=int, default=0, choices=[0, 4, 8, 16],
-                    help="horizon chunks per instance of the batched solve (0: autotune over 4, 8, 16)")
+    ap.add_argument("--warps", type=int, default=0, choices=[0, 1, 4, 8, 16],
+                    help="horizon chunks per instance of the batched solve (0: autotune over "
+                         "1 = the sequential recursion and the scan's 4, 8, 16)")
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--comparator-sample", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -797,11 +934,16 @@ def main():
                     help="skip the whole-body LQ batch and single-LQR measurements")
     ap.add_argument("--sweep", action="store_true",
                     help="print the horizon / robot-count latency sweep instead of the bench line")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the measured FFMA, DFMA and TF32 tensor-core peaks instead")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.sweep:
         print(json.dumps(run_sweep(args)), flush=True)
+        return
+    if args.peaks:
+        print(json.dumps(run_peaks(args)), flush=True)
         return
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:

@@ -64,7 +64,11 @@ PDILQR_API const char *pdilqr_status_string(int status);
 
 /* ------------------------------------------------------------- batches */
 
-/* Host-side description of a batch (copied by pdilqr_plan_create). */
+/* Host-side description of a batch (copied by pdilqr_plan_create).  One
+ * plan serves one (n, m): the kernels are compiled per size, so a batch of
+ * mixed sizes is solved through one plan per size (the server's size classes
+ * do exactly that).  The problem statement of Sec. II-A/II-B fixes n and m per
+ * problem; nothing in the method couples instances of different sizes. */
 typedef struct {
     int32_t n;                 /* state dimension  (same for every instance)   */
     int32_t m;                 /* control dimension                             */
@@ -88,14 +92,27 @@ typedef struct pdilqr_plan pdilqr_plan;
 
 /* Validate a batch, copy its description to the current CUDA device and
  * allocate the plan's workspace (device memory, about (2n^2 + nm + 3n + m)
- * floats per stage slot).  Supported (n, m): (1,1) (2,1) (3,2) (4,2) (12,12)
- * and, for the Riccati comparator only, (36,24).  Errors: INVALID_ARG,
- * NO_MEMORY, CUDA.  *out is NULL on error. */
+ * floats per stage slot).  Supported (n, m): (1,1) (2,1) (3,2) (4,2),
+ * (36,24) (the whole-body-sized LQ problem), and the SRBD sizes
+ * (12 R, 12 R) for R = 1, 2, 4, 8, 16 robots, which also have the
+ * linearisation, the merit and the fused SQP.  Every size has both the scan
+ * and the Riccati solvers.  Errors: INVALID_ARG, NO_MEMORY, CUDA.  *out is
+ * NULL on error. */
 PDILQR_API pdilqr_status pdilqr_plan_create(const pdilqr_batch *batch, const pdilqr_opts *opts,
                                  pdilqr_plan **out);
 PDILQR_API pdilqr_status pdilqr_plan_destroy(pdilqr_plan *plan);
 /* Warps per instance the plan uses for the scan (after the 0 -> pick rule). */
 PDILQR_API int32_t pdilqr_plan_warps(const pdilqr_plan *plan);
+
+/* Test switches of a plan (0 = none, the default).  They exist to exercise
+ * failure handling without faulting the GPU and are never needed otherwise.
+ *   PDILQR_DEBUG_TC_SKIP_ISSUE: the tensor-core products (one-chunk kernels of
+ *   n >= 96) issue neither their MMAs nor the commit that signals them, so the
+ *   bounded wait for them runs out (after about 0.6 s per CTA); the instance
+ *   then ends with status PDILQR_E_TIMEOUT and the context stays usable.
+ * Errors: INVALID_ARG (unknown bits). */
+#define PDILQR_DEBUG_TC_SKIP_ISSUE 1
+PDILQR_API pdilqr_status pdilqr_plan_set_debug(pdilqr_plan *plan, int32_t flags);
 
 /* ------------------------------------------------------- LQ KKT solves */
 
@@ -152,7 +169,10 @@ PDILQR_API pdilqr_status pdilqr_kkt_residual(pdilqr_plan *plan, const pdilqr_lq 
  * The caller passes inputs and outputs as in pdilqr_kkt_scan_solve, plus the
  * batch tables as DEVICE arrays N [count] and stage_off [count] and the
  * number of stage slots total_stages (>= max(stage_off + N + 1)); warps is
- * 4, 8, 16 or 0 (= 8).  Batches needing more than
+ * 4, 8, 16 or 0 (= 8).  The instances' slot ranges [stage_off_i,
+ * stage_off_i + N_i] must be disjoint, as for pdilqr_kkt_scan_solve: they
+ * live in device memory, so this call cannot check it, and overlapping
+ * ranges race on the scratch and on dx, du, dlam.  Batches needing more than
  * pdilqr_noalloc_capacity_stages(n, m) stage slots are rejected with
  * PDILQR_E_INVALID_ARG before any GPU work; an instance whose slots fall
  * outside total_stages gets status PDILQR_E_INVALID_ARG and is skipped.  No

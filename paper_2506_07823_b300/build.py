@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libpdilqr.so")
 SOURCES = ["pdilqr.cu", "serve.cu", "ops_small.cu", "ops_12.cu", "ops_24.cu", "ops_36.cu",
-           "ops_48.cu", "ops_96.cu", "ops_192.cu"]
+           "ops_48.cu", "ops_96.cu", "ops_192.cu", "peaks.cu"]
 BUILD_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

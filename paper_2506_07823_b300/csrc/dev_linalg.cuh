@@ -133,14 +133,45 @@ struct TcCtx {
     uint32_t ncols;    // columns allocated (TMEM_TILE per 128-row tile)
     uint32_t phase;    // parity the next wait expects
     int failed;        // a wait ran out (the products written as NaN)
+    int skip_issue;    // test switch: issue neither the MMAs nor their commit,
+                       // so that the bounded wait runs out with nothing in flight
 };
+
+// Limits of the wait for a batch of MMAs (which completes in microseconds):
+// the wait itself, and the second wait for MMAs still in flight after it ran
+// out, before the staging buffers and the tensor memory are reused or freed.
+constexpr uint64_t kTcWaitNs = 500000000ull;
+constexpr uint64_t kTcDrainNs = 100000000ull;
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Poll phase `phase` of an mbarrier until it completes or limit_ns pass (also
+// capped in polls); returns whether it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase, uint64_t limit_ns)
+{
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 28); ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"((uint32_t)__cvta_generic_to_shared(mbar)), "r"(phase) : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Allocate ncols columns (TMEM_TILE per 128-row tile of the largest
 // product; a power of two, at most 512) and set up the barrier (all threads
 // of the CTA).
-__device__ __forceinline__ void tc_setup(TcCtx* c, uint32_t ncols)
+__device__ __forceinline__ void tc_setup(TcCtx* c, uint32_t ncols, bool skip_issue = false)
 {
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -152,6 +183,7 @@ __device__ __forceinline__ void tc_setup(TcCtx* c, uint32_t ncols)
         c->ncols = ncols;
         c->phase = 0;
         c->failed = 0;
+        c->skip_issue = skip_issue ? 1 : 0;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -403,7 +435,7 @@ __device__ void mm_tc(const Grp<NT>& g, float* out, int ldo, const float* A, int
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         g.sync();
-        if (t == 0 && !failed) {
+        if (t == 0 && !failed && !cx->skip_issue) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int mt = 0; mt < MT; ++mt) {
                 const uint32_t d = tmem + (uint32_t)(mt * TMEM_TILE);
@@ -420,16 +452,18 @@ __device__ void mm_tc(const Grp<NT>& g, float* out, int ldo, const float* A, int
                          :: "r"(smem_u32(&cx->mbar)) : "memory");
         }
         if (!failed) {
-            uint32_t done = 0;
-            for (int it = 0; it < (1 << 22) && !done; ++it)
-                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                             " selp.u32 %0, 1, 0, p;\n}"
-                             : "=r"(done) : "r"(smem_u32(&cx->mbar)), "r"(phase) : "memory");
-            failed = done == 0;
+            const bool done = mbar_wait_bounded(&cx->mbar, phase, kTcWaitNs);
+            // one verdict for the whole CTA (the group is the CTA), so that
+            // the TMEM loads below run on all warps or on none
+            failed = __syncthreads_or(done ? 0 : 1) != 0;
+            // MMAs possibly still in flight get a second bounded wait before
+            // their operands and accumulators are given up
+            if (failed && !done) mbar_wait_bounded(&cx->mbar, phase, kTcDrainNs);
             phase ^= 1;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         g.sync();
+        if (failed) break;   // uniform: no further chunk is staged or issued
     }
     // read the accumulators back: out = D + sgn * acc.  A lane holds one row
     // of a warp's 32 x 16 slice; the slice goes through the (now idle)

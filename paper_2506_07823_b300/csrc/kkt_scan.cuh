@@ -33,11 +33,21 @@
 #pragma once
 
 #include "dev_linalg.cuh"
+#include "pdilqr.h"
 
 namespace pdl {
 
-// Status codes written per instance (mirror the C ABI's pdilqr_status).
-enum : int32_t { ST_OK = 0, ST_NOT_SPD = 2, ST_SINGULAR = 3, ST_NONFINITE = 4 };
+// Status codes written per instance (the C ABI's pdilqr_status values).
+enum : int32_t {
+    ST_OK = PDILQR_OK,
+    ST_INVALID_ARG = PDILQR_E_INVALID_ARG,
+    ST_NOT_SPD = PDILQR_E_NOT_SPD,
+    ST_SINGULAR = PDILQR_E_SINGULAR,
+    ST_NONFINITE = PDILQR_E_NONFINITE,
+    ST_TIMEOUT = PDILQR_E_TIMEOUT
+};
+static_assert(ST_INVALID_ARG == 1 && ST_NONFINITE == 4 && ST_TIMEOUT == 5,
+              "per-instance status words carry the C ABI's codes");
 
 struct KktArgs {
     const float *A, *B, *c, *Q, *R, *S, *q, *r;  // LQ data; S may be null (S = 0)
@@ -52,6 +62,7 @@ struct KktArgs {
     int count;
     float* gws;                                  // per-CTA work areas in global memory
                                                  // (sizes whose areas exceed shared memory)
+    int dbg;                                     // test switches (PDILQR_DEBUG_*), normally 0
 };
 
 // ------------------------------------------------------------------ layouts
@@ -523,12 +534,15 @@ __device__ __forceinline__ void roll_fetch(const Grp<NT>& g, float* b, const Kkt
     cp_async_commit();
 }
 
+// Returns false on a thread that wrote a non-finite dx, du or dlam (a NaN or
+// Inf anywhere in the inputs reaches these outputs).
 template <int NX, int NU, int NT>
-__device__ void rollout_chunk(const Grp<NT>& g, float* x, float* xn, float* buf, const KktArgs& a,
+__device__ bool rollout_chunk(const Grp<NT>& g, float* x, float* xn, float* buf, const KktArgs& a,
                               int64_t off, int N, int k0, int k1)
 {
     using L = RollL<NX, NU>;
-    if (k0 >= k1) return;
+    if (k0 >= k1) return true;
+    bool fin = true;
     roll_fetch<NX, NU, NT>(g, buf, a, off + k0, k0 == N);
     for (int k = k0; k < k1; ++k) {
         const int64_t gs = off + k;
@@ -540,18 +554,24 @@ __device__ void rollout_chunk(const Grp<NT>& g, float* x, float* xn, float* buf,
             cp_async_wait<0>();
         }
         g.sync();
-        for (int i = g.t; i < NX; i += NT) a.dx[gs * NX + i] = x[i];
+        for (int i = g.t; i < NX; i += NT) {
+            a.dx[gs * NX + i] = x[i];
+            fin = fin && isfinite(x[i]);
+        }
         mv<NX, NX, false, NT, false>(g, a.dlam + gs * NX, cur + L::P, NX, x, cur + L::p);
         if (k < N) {
             mv<NU, NX, false, NT, false>(g, a.du + gs * NU, cur + L::K, NX, x, cur + L::k);
             mv<NX, NX, false, NT, false>(g, xn, cur + L::Ab, NX, x, cur + L::bb);
             g.sync();
             for (int i = g.t; i < NX; i += NT) x[i] = xn[i];
+            for (int i = g.t; i < NU; i += NT) fin = fin && isfinite(a.du[gs * NU + i]);
         } else {
             for (int i = g.t; i < NU; i += NT) a.du[gs * NU + i] = 0.f;
         }
         g.sync();
+        for (int i = g.t; i < NX; i += NT) fin = fin && isfinite(a.dlam[gs * NX + i]);
     }
+    return fin;
 }
 
 // ---------------------------------------------------------- chunk partition
@@ -597,6 +617,10 @@ struct ScanSmem {
     static constexpr int XS = W * round4(NX);
     static constexpr int TOTAL = SLOTS + W * PRIV + XS + 4;  // + status words
     static constexpr size_t BYTES = sizeof(float) * TOTAL;
+    // phase 3 reads the boundary value function [P | p] (ends before ELEM) at
+    // the start of the next chunk's private area while that chunk writes its
+    // own v0 at STG: the two ranges must not overlap
+    static_assert(ELEM <= STG, "boundary value function and v0 overlap");
 };
 
 // Tile buffers of the wide units (one TileBuf per unit), placed after a
@@ -833,10 +857,12 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         float* rb = priv + 2 * round4(NX);
         for (int i = g.t; i < NX; i += NT) x[i] = xs[warp * round4(NX) + i];
         g.sync();
-        rollout_chunk<NX, NU, NT>(g, x, xn, rb, a, off, N, k0, k1);
+        if (!rollout_chunk<NX, NU, NT>(g, x, xn, rb, a, off, N, k0, k1)) atomicMax(st_word, ST_NONFINITE);
     }
     __syncthreads();
-    const int status = st_word[0];
+    int status = st_word[0];
+    // a tensor-core product whose bounded wait ran out (uniform over the CTA)
+    if (tc && tc->failed) status = ST_TIMEOUT;
     __syncthreads();
     return status;
 }
@@ -877,7 +903,7 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     if constexpr (UseTc<NX, NU, W, UW>::value) {
         __shared__ TcCtx tcx;
         if (factors) {
-            tc_setup(&tcx, UseTc<NX, NU, W, UW>::cols);
+            tc_setup(&tcx, UseTc<NX, NU, W, UW>::cols, (a.dbg & PDILQR_DEBUG_TC_SKIP_ISSUE) != 0);
             tc = &tcx;
         }
     }
@@ -902,7 +928,7 @@ __global__ void __launch_bounds__(W * 32, MinBlocks<W>::value)
     const int N = a.N[inst];
     const int64_t off = a.off[inst];
     if (N < 1 || N > 4096 || off < 0 || off + N + 1 > limit) {
-        if (threadIdx.x == 0) a.status[inst] = 1;  // invalid argument
+        if (threadIdx.x == 0) a.status[inst] = ST_INVALID_ARG;
         return;
     }
     const LqSource src(a);
@@ -954,7 +980,8 @@ __global__ void __launch_bounds__(128) riccati_kernel(const __grid_constant__ Kk
     __threadfence_block();
     for (int i = g.t; i < NX; i += 32) x[i] = a.s[(int64_t)inst * NX + i];
     g.sync();
-    rollout_chunk<NX, NU, 32>(g, x, xn, rb, a, off, N, 0, N + 1);
+    const bool fin = rollout_chunk<NX, NU, 32>(g, x, xn, rb, a, off, N, 0, N + 1);
+    if (__any_sync(0xffffffffu, !fin)) bad = ST_NONFINITE;
     if (g.t == 0) a.status[inst] = bad;
 }
 

@@ -3,6 +3,8 @@
 // launcher reports cudaErrorInvalidConfiguration.
 #pragma once
 
+#include <atomic>
+
 #include "ops.h"
 
 namespace pdl {
@@ -13,6 +15,24 @@ template <class Kern>
 static cudaError_t set_smem(Kern kernel, size_t bytes)
 {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// The shared-memory opt-in is an attribute of the kernel on each device: it
+// is set once per (kernel, device) and remembered in a per-kernel bit mask
+// of devices.  Setting it is idempotent, so two threads that race on the
+// first launch on a device at worst both set it; the bit is published only
+// after the call succeeded.
+template <class Kern>
+static cudaError_t ensure_smem(Kern kernel, size_t bytes, std::atomic<uint64_t>& done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = set_smem(kernel, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
 }
 
 
@@ -32,12 +52,9 @@ static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
         constexpr size_t tb = UnitTiles<W, UW>::total(GWS ? 0 : SM::BYTES);
         constexpr size_t bytes = GWS ? UnitFactor<NU, W, UW>::total(tb) : tb;
         if (GWS && !a.gws) return cudaErrorInvalidConfiguration;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t e = set_smem(kkt_scan_kernel<NX, NU, W, UW>, bytes);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        static std::atomic<uint64_t> smem_done{0};
+        if (cudaError_t e = ensure_smem(kkt_scan_kernel<NX, NU, W, UW>, bytes, smem_done); e != cudaSuccess)
+            return e;
         KktArgs b = a;
         if (!GWS) b.gws = nullptr;
         kkt_scan_kernel<NX, NU, W, UW><<<a.count, W * 32 * UW, bytes, st>>>(b);
@@ -52,12 +69,9 @@ static cudaError_t launch_scan_checked_w(const KktArgs& a, int64_t limit, cudaSt
     if constexpr (SM::BYTES > kSmemMax) {
         return cudaErrorInvalidConfiguration;
     } else {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = set_smem(kkt_scan_checked_kernel<NX, NU, W>, SM::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> smem_done{0};
+    if (cudaError_t e = ensure_smem(kkt_scan_checked_kernel<NX, NU, W>, SM::BYTES, smem_done); e != cudaSuccess)
+        return e;
     kkt_scan_checked_kernel<NX, NU, W><<<a.count, W * 32, SM::BYTES, st>>>(a, limit);
     return cudaGetLastError();
     }
@@ -131,12 +145,9 @@ static cudaError_t launch_riccati(const KktArgs& a, cudaStream_t st)
     if constexpr (bytes > kSmemMax) {
         return cudaErrorInvalidConfiguration;
     } else {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = set_smem(riccati_kernel<NX, NU>, bytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> smem_done{0};
+    if (cudaError_t e = ensure_smem(riccati_kernel<NX, NU>, bytes, smem_done); e != cudaSuccess)
+        return e;
     const int grid = (a.count + WPB - 1) / WPB;
     riccati_kernel<NX, NU><<<grid, 32 * WPB, bytes, st>>>(a);
     return cudaGetLastError();
@@ -183,12 +194,9 @@ static cudaError_t launch_linearize(const LinArgs& a, cudaStream_t st)
         return cudaGetLastError();
     } else {
         constexpr size_t bytes = C::SPB * C::STAGE_BYTES;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t e = set_smem(linearize_kernel<NX, NU, C::SPB, C::UW>, bytes);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        static std::atomic<uint64_t> smem_done{0};
+        if (cudaError_t e = ensure_smem(linearize_kernel<NX, NU, C::SPB, C::UW>, bytes, smem_done); e != cudaSuccess)
+            return e;
         LinArgs b = a;
         b.work = nullptr;
         const int64_t blocks = (a.total + C::SPB - 1) / C::SPB;
@@ -218,12 +226,9 @@ static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
         constexpr size_t tb = UnitTiles<W, UW>::total(GWS ? SM::EXTRA_BYTES : SM::BYTES);
         constexpr size_t bytes = GWS ? UnitFactor<NU, W, UW>::total(tb) : tb;
         if (GWS && !a.ka.gws) return cudaErrorInvalidConfiguration;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t e = set_smem(sqp_kernel<NX, NU, W, UW>, bytes);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        static std::atomic<uint64_t> smem_done{0};
+        if (cudaError_t e = ensure_smem(sqp_kernel<NX, NU, W, UW>, bytes, smem_done); e != cudaSuccess)
+            return e;
         SqpArgs b = a;
         if (!GWS) b.ka.gws = nullptr;
         sqp_kernel<NX, NU, W, UW><<<a.ka.count, W * 32 * UW, bytes, st>>>(b);

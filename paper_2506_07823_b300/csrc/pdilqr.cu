@@ -157,6 +157,13 @@ extern "C" pdilqr_status pdilqr_plan_destroy(pdilqr_plan* pl)
 
 extern "C" int32_t pdilqr_plan_warps(const pdilqr_plan* pl) { return pl ? pl->warps : 0; }
 
+extern "C" pdilqr_status pdilqr_plan_set_debug(pdilqr_plan* pl, int32_t flags)
+{
+    if (!pl || (flags & ~PDILQR_DEBUG_TC_SKIP_ISSUE)) return PDILQR_E_INVALID_ARG;
+    pl->dbg = flags;
+    return PDILQR_OK;
+}
+
 // ------------------------------------------------------------- KKT solves
 static KktArgs make_args(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s, float* dx,
                          float* du, float* dl, float* K, float* k, float* P, float* p,
@@ -179,6 +186,7 @@ static KktArgs make_args(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s, f
     a.status = status;
     a.count = pl->count;
     a.gws = pl->gws;
+    a.dbg = pl->dbg;
     return a;
 }
 
@@ -209,6 +217,13 @@ static pdilqr_status residual_into(pdilqr_plan* pl, const pdilqr_lq* lq, const f
     return PDILQR_OK;
 }
 
+// status[i] = max(status[i], st2[i]): the correction solve's verdict joins the first one's
+__global__ void status_merge_kernel(int32_t* status, const int32_t* st2, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count && st2[i] > status[i]) status[i] = st2[i];
+}
+
 static cudaError_t launch_axpy(float* z, const float* dz, int64_t n, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
@@ -237,6 +252,8 @@ static pdilqr_status solve_common(pdilqr_plan* pl, const pdilqr_lq* lq, const fl
         KktArgs b = make_args(pl, &corr, pl->rs, pl->ddx, pl->ddu, pl->ddl, nullptr, nullptr,
                               nullptr, nullptr, pl->st2);
         PD_CUDA(run(b));
+        status_merge_kernel<<<(pl->count + 255) / 256, 256, 0, st>>>(out->status, pl->st2, pl->count);
+        PD_CUDA(cudaGetLastError());
         const int64_t T = pl->total;
         PD_CUDA(launch_axpy(out->dx, pl->ddx, T * pl->n, st));
         PD_CUDA(launch_axpy(out->du, pl->ddu, T * pl->m, st));
@@ -435,6 +452,7 @@ extern "C" pdilqr_status pdilqr_kkt_scan_solve_noalloc(
     a.status = status;
     a.count = count;
     a.gws = nullptr;
+    a.dbg = 0;
     PD_CUDA(ops->scan_checked(a, warps, total_stages, (cudaStream_t)stream));
     return PDILQR_OK;
 }

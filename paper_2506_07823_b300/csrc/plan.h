@@ -27,6 +27,7 @@ struct pdilqr_plan {
     float* gws = nullptr;       // per-CTA scan work areas (sizes beyond shared memory)
     float* lin_ws = nullptr;    // stage areas of the standalone linearisation (large sizes)
     int max_count = 0;   // capacity of the batch tables (capacity plans)
+    int dbg = 0;         // test switches (PDILQR_DEBUG_*)
 
     template <typename T>
     cudaError_t alloc(T** ptr, size_t count_) {

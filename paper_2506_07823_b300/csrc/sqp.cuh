@@ -10,7 +10,7 @@
 
 namespace pdl {
 
-enum : int32_t { ST_LINESEARCH = 8 };
+enum : int32_t { ST_LINESEARCH = PDILQR_E_LINESEARCH };
 
 struct SqpArgs {
     pdilqr_srbd_model md;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     if constexpr (UseTc<NX, NU, W, UW>::value) {
         __shared__ TcCtx tcx;
         if (factors) {
-            tc_setup(&tcx, UseTc<NX, NU, W, UW>::cols);
+            tc_setup(&tcx, UseTc<NX, NU, W, UW>::cols, (a.ka.dbg & PDILQR_DEBUG_TC_SKIP_ISSUE) != 0);
             tc = &tcx;
         }
     }

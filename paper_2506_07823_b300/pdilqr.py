@@ -111,6 +111,8 @@ _lib.pdilqr_plan_create.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Opts
 _lib.pdilqr_plan_destroy.argtypes = [_vp]
 _lib.pdilqr_plan_warps.argtypes = [_vp]
 _lib.pdilqr_plan_warps.restype = ctypes.c_int32
+_lib.pdilqr_plan_set_debug.argtypes = [_vp, ctypes.c_int32]
+DEBUG_TC_SKIP_ISSUE = 1
 for _f in ("pdilqr_kkt_scan_solve", "pdilqr_riccati_solve"):
     getattr(_lib, _f).argtypes = [_vp, ctypes.POINTER(_LQ), _vp, ctypes.POINTER(_KktOut), _vp]
 _lib.pdilqr_kkt_residual.argtypes = [_vp, ctypes.POINTER(_LQ), _vp, _vp, _vp, _vp, _vp, _vp]
@@ -127,6 +129,19 @@ _lib.pdilqr_kkt_scan_solve_noalloc.argtypes = [
     ctypes.POINTER(_LQ), _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.pdilqr_noalloc_capacity_stages.argtypes = [ctypes.c_int32, ctypes.c_int32]
 _lib.pdilqr_noalloc_capacity_stages.restype = ctypes.c_int64
+_lib.pdilqr_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
+
+PEAK_FFMA, PEAK_DFMA, PEAK_TF32_MMA = 0, 1, 2
+
+
+def peak_probe(kind: int, reps: int = 3) -> tuple[float, float]:
+    """Measured peak rate of one pipe on the current device (pdilqr_peak_probe):
+    (TFLOP/s, ms of the best launch)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.pdilqr_peak_probe(int(kind), int(reps), ctypes.byref(tf), ctypes.byref(ms)),
+           "pdilqr_peak_probe")
+    return tf.value, ms.value
 
 
 def noalloc_capacity_stages(n: int, m: int) -> int:
@@ -199,6 +214,10 @@ class Plan:
                "pdilqr_plan_create")
         self._h = h
         self.warps = int(_lib.pdilqr_plan_warps(h))
+
+    def set_debug(self, flags: int):
+        """Test switches of the plan (``DEBUG_TC_SKIP_ISSUE``); 0 clears them."""
+        _check(_lib.pdilqr_plan_set_debug(self._h, int(flags)), "pdilqr_plan_set_debug")
 
     def close(self):
         if getattr(self, "_h", None):
@@ -431,6 +450,10 @@ class Server:
         st = _ServeStats()
         _check(_lib.pdilqr_serve_stats(self._h, ctypes.byref(st)), "pdilqr_serve_stats")
         return {k: getattr(st, k) for k, _ in _ServeStats._fields_}
+
+    def set_debug(self, flags: int):
+        """Test switches of the plan (``DEBUG_TC_SKIP_ISSUE``); 0 clears them."""
+        _check(_lib.pdilqr_plan_set_debug(self._h, int(flags)), "pdilqr_plan_set_debug")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -236,3 +236,27 @@ def test_batch_alone_equals_in_mix():
     sl = slice(int(off[i]), int(off[i]) + int(Nv[i]) + 1)
     assert torch.equal(mix["dx"][sl], alone["dx"])
     assert torch.equal(mix["dlam"][sl], alone["dlam"])
+
+
+@pytest.mark.parametrize("solver", ["scan", "riccati"])
+@pytest.mark.parametrize("n,m", [(4, 2), (12, 12), (36, 24)])
+def test_nonfinite_status(solver, n, m):
+    """A NaN in one instance's gradient q_k, or an Inf in another's initial
+    defect, is reported as E_NONFINITE for that instance only; the other
+    instances of the batch keep their solution."""
+    insts, packed, Nv, off, s = make_batch(n, m, [9, 12, 20, 7], seed=13)
+    packed["q"][off[1] + 4, 0] = np.nan
+    s = s.copy()
+    s[3, 0] = np.inf
+    from paper_2506_07823_b300.pdilqr import Plan, E_NONFINITE
+    plan = Plan(n, m, Nv, off, warps=4)
+    lq, sd = to_dev(packed, s, False)
+    fn = plan.kkt_scan_solve if solver == "scan" else plan.riccati_solve
+    out = fn(lq, sd)
+    torch.cuda.synchronize()
+    st = out["status"].cpu().numpy()
+    assert st[1] == E_NONFINITE and st[3] == E_NONFINITE, st
+    keep = [0, 2]
+    sub = {k: out[k] for k in ("dx", "du", "dlam")}
+    sub["status"] = out["status"][keep]
+    check_parity([insts[i] for i in keep], Nv[keep], off[keep], sub, s[keep], False)

@@ -224,3 +224,89 @@ def test_sqp_parity_multi_robot(nrob, warps):
         assert rel(us[o:o + N], ur[:N]) <= REL_TOL, rel(us[o:o + N], ur[:N])
         assert rel(ls[sl], lr) <= REL_TOL, rel(ls[sl], lr)
         assert abs(info["J"][i].item() - inf["J"]) <= 1e-4 * abs(inf["J"])
+
+
+@pytest.mark.parametrize("mode", ["replay", "free"])
+def test_sqp_parity_long_horizon(mode):
+    """The horizon sweep's longest problems (N = 150 and 200, one robot) through
+    the 16-chunk fused SQP, 10 iterations."""
+    from paper_2506_07823_b300 import pdilqr
+    iters = 10
+    insts, packed, Nv, off, x0 = srbd_case(2, 61, [150, 200])
+    prm = synth.srbd_params()
+    refs = [run_oracle(prm, pr, iters) for pr in insts]
+    d = dev(packed)
+    plan = pdilqr.Plan(12, 12, Nv, off, warps=16)
+    replay = None
+    if mode == "replay":
+        replay = torch.tensor(np.stack([r[3]["alpha"] for r in refs]).astype(np.float32), device="cuda")
+    info = plan.solve(pdilqr.srbd_model(prm), torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                      d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                      max_iters=iters, alpha_replay=replay)
+    torch.cuda.synchronize()
+    assert np.all(info["status"].cpu().numpy() == 0)
+    xs, us, ls = (d[k].double().cpu().numpy() for k in ("x", "u", "lam"))
+    for i, (xr, ur, lr, inf) in enumerate(refs):
+        N, o = int(Nv[i]), int(off[i])
+        sl = slice(o, o + N + 1)
+        assert rel(xs[sl], xr) <= REL_TOL, rel(xs[sl], xr)
+        assert rel(us[o:o + N], ur[:N]) <= REL_TOL, rel(us[o:o + N], ur[:N])
+        assert rel(ls[sl], lr) <= REL_TOL, rel(ls[sl], lr)
+
+
+@pytest.mark.parametrize("warps", [1, 4])
+@pytest.mark.parametrize("nrob", [8, 16])
+def test_sqp_parity_multi_robot_horizon50(nrob, warps):
+    """Centralised 8- and 16-robot problems at the serving horizon N = 50:
+    the one-chunk recursion (tensor-core products) and the 4-chunk scan from
+    the global workspace, replaying the oracle's step sizes."""
+    from paper_2506_07823_b300 import pdilqr
+    n = 12 * nrob
+    iters = 2
+    pr = synth.srbd_problem(50, seed=700 + nrob, nrob=nrob)
+    packed, Nv, off = synth.pack([pr], synth.SRBD_KEYS)
+    prm = synth.srbd_params(nrob)
+    xr, ur, lr, inf = run_oracle(prm, pr, iters)
+    d = dev(packed)
+    plan = pdilqr.Plan(n, n, Nv, off, warps=warps)
+    replay = torch.tensor(inf["alpha"][None].astype(np.float32), device="cuda")
+    info = plan.solve(pdilqr.srbd_model(prm),
+                      torch.tensor(pr["x0hat"][None], dtype=torch.float32, device="cuda"),
+                      d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                      max_iters=iters, alpha_replay=replay)
+    torch.cuda.synchronize()
+    assert info["status"].item() == 0
+    assert info["iters"].item() == iters
+    xs, us, ls = (d[k].double().cpu().numpy() for k in ("x", "u", "lam"))
+    assert rel(xs, xr) <= REL_TOL, rel(xs, xr)
+    assert rel(us[:50], ur[:50]) <= REL_TOL, rel(us[:50], ur[:50])
+    assert rel(ls, lr) <= REL_TOL, rel(ls, lr)
+
+
+def test_tensor_core_wait_timeout_status():
+    """The bounded wait of the tensor-core products: with the test switch that
+    issues no MMA (so nothing ever signals the barrier) the instance ends with
+    E_TIMEOUT instead of hanging; the context stays usable and the next solve
+    of the same plan is correct."""
+    from paper_2506_07823_b300 import pdilqr
+    nrob, iters = 8, 1
+    pr = synth.srbd_problem(3, seed=77, nrob=nrob)
+    packed, Nv, off = synth.pack([pr], synth.SRBD_KEYS)
+    prm = synth.srbd_params(nrob)
+    x0 = torch.tensor(pr["x0hat"][None], dtype=torch.float32, device="cuda")
+    plan = pdilqr.Plan(96, 96, Nv, off, warps=1)
+    d = dev(packed)
+    plan.set_debug(pdilqr.DEBUG_TC_SKIP_ISSUE)
+    info = plan.solve(pdilqr.srbd_model(prm), x0, d["x"], d["u"], d["lam"], d["xref"],
+                      d["uref"], d["contact"], max_iters=iters)
+    torch.cuda.synchronize()
+    assert info["status"].item() == pdilqr.E_TIMEOUT
+    plan.set_debug(0)
+    xr, ur, lr, inf = run_oracle(prm, pr, iters)
+    d = dev(packed)
+    replay = torch.tensor(inf["alpha"][None].astype(np.float32), device="cuda")
+    info = plan.solve(pdilqr.srbd_model(prm), x0, d["x"], d["u"], d["lam"], d["xref"],
+                      d["uref"], d["contact"], max_iters=iters, alpha_replay=replay)
+    torch.cuda.synchronize()
+    assert info["status"].item() == 0
+    assert rel(d["x"].double().cpu().numpy(), xr) <= REL_TOL
