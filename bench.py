@@ -142,6 +142,10 @@ def oracle_run(pool, cores: int, insts: list, keep: bool = False):
     return its, secs, kept
 
 
+# oracle status codes (0 ok, 1 no step accepted, 2 not SPD) as the C ABI's
+ORACLE_STATUS = {0: 0, 1: 8, 2: 2}
+
+
 def compare_with_oracle(kept, Nv, off, x, u, lam, status, alpha) -> dict:
     """Final iterates of the timed batch against the oracle's free-running
     solves of the same instances: status agreement, and per block
@@ -153,6 +157,7 @@ def compare_with_oracle(kept, Nv, off, x, u, lam, status, alpha) -> dict:
     err_same = {"x": [], "u": [], "lam": []}
     for idx, xr, ur, lr, st_o, al_o in kept:
         st_g = int(status[idx])
+        st_o = ORACLE_STATUS.get(st_o, st_o)
         key = f"gpu{st_g}_oracle{st_o}"
         agree[key] = agree.get(key, 0) + 1
         if st_g != 0 or st_o != 0:
@@ -443,6 +448,7 @@ def run_gpu(args):
                              f"SQP solve each, FP64 C oracle, {cores} processes, {secs:.1f} s"}
             vs_oracle = compare_with_oracle(kept, Nv, off, final["x"], final["u"], final["lam"],
                                             st, alpha_gpu)
+            vs_oracle["replay"] = replay_check(torch, plan, md, work, base, kept, Nv, off)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -487,6 +493,44 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def replay_check(torch, plan, md, work, base, kept, Nv, off) -> dict:
+    """The benchmarked solver once more on the same batch (untimed), each
+    instance taking the oracle's step sizes (the replay mode of the parity
+    tests), so that every instance follows the oracle's path: per block
+    relative error of the final iterate over the instances the oracle solves
+    with status OK, and how many are within 1e-4."""
+    count = plan.count
+    alpha = np.ones((count, ITERS), np.float32)
+    for idx, _, _, _, _, al_o in kept:
+        alpha[idx] = al_o
+    dev = work["x"].device
+    inf = {"iters": torch.zeros(count, device=dev, dtype=torch.int32),
+           "status": torch.zeros(count, device=dev, dtype=torch.int32),
+           "alpha": None, "J": None, "theta": None}
+    for k in ("x", "u", "lam"):
+        work[k].copy_(base[k])
+    plan.solve(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"], work["uref"],
+               work["contact"], max_iters=ITERS, alpha_replay=torch.tensor(alpha, device=dev),
+               info=inf)
+    torch.cuda.synchronize()
+    x, u, lam = (work[k].double().cpu().numpy() for k in ("x", "u", "lam"))
+    st = inf["status"].cpu().numpy()
+    errs, worst, status_match = [], {"x": 0.0, "u": 0.0, "lam": 0.0}, 0
+    for idx, xr, ur, lr, st_o, _ in kept:
+        status_match += int(int(st[idx]) == ORACLE_STATUS.get(st_o, st_o))
+        if st_o != 0 or st[idx] != 0:
+            continue
+        N, o = int(Nv[idx]), int(off[idx])
+        e = {"x": np.abs(x[o:o + N + 1] - xr).max() / max(np.abs(xr).max(), 1e-30),
+             "u": np.abs(u[o:o + N] - ur[:N]).max() / max(np.abs(ur[:N]).max(), 1e-30),
+             "lam": np.abs(lam[o:o + N + 1] - lr).max() / max(np.abs(lr).max(), 1e-30)}
+        for k in e:
+            worst[k] = max(worst[k], float(e[k]))
+        errs.append(max(e.values()))
+    return {"instances": len(errs), "status_match": status_match, "max_rel_err": worst,
+            "within_1e-4": int(sum(v <= 1e-4 for v in errs))}
 
 
 def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, plans, args):
