@@ -117,7 +117,9 @@ def _oracle_worker(args):
                                           pr["xref"], pr["uref"], pr["contact"], max_iters=ITERS)
         its += info["iters"]
         if keep:
-            kept.append((idx, x, u, lam, int(info["status"]), np.asarray(info["alpha"][:ITERS])))
+            al = np.zeros(ITERS)
+            al[:min(ITERS, len(info["alpha"]))] = np.asarray(info["alpha"][:ITERS])
+            kept.append((idx, x, u, lam, int(info["status"]), al))
     return its, kept
 
 
@@ -518,9 +520,13 @@ def replay_check(torch, plan, md, work, base, kept, Nv, off) -> dict:
     x, u, lam = (work[k].double().cpu().numpy() for k in ("x", "u", "lam"))
     st = inf["status"].cpu().numpy()
     errs, worst, status_match = [], {"x": 0.0, "u": 0.0, "lam": 0.0}, 0
-    for idx, xr, ur, lr, st_o, _ in kept:
-        status_match += int(int(st[idx]) == ORACLE_STATUS.get(st_o, st_o))
-        if st_o != 0 or st[idx] != 0:
+    for idx, xr, ur, lr, st_o, al_o in kept:
+        # an oracle run that stopped early (converged at its precision floor)
+        # replays as a zero step, which the GPU reports as E_LINESEARCH with
+        # the iterate left where the oracle stopped
+        stopped = st_o == 0 and bool(np.any(al_o == 0.0)) and int(st[idx]) == 8
+        status_match += int(int(st[idx]) == ORACLE_STATUS.get(st_o, st_o) or stopped)
+        if st_o != 0 or (st[idx] != 0 and not stopped):
             continue
         N, o = int(Nv[idx]), int(off[idx])
         e = {"x": np.abs(x[o:o + N + 1] - xr).max() / max(np.abs(xr).max(), 1e-30),

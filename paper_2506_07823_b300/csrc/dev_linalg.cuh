@@ -85,9 +85,12 @@ struct Grp {
     float* fb = nullptr;  // the group's shared-memory factor buffer, or none
     int fbn = 0;          // its size in floats
     struct TcCtx* tc = nullptr;  // tensor-core context of the CTA (TMEM, barrier), or none
+    unsigned mask = 0xffffffffu; // lanes of a group narrower than a warp (NT = 16: one half)
     __device__ __forceinline__ void sync() const {
         if constexpr (NT == 32) {
             __syncwarp();
+        } else if constexpr (NT == 16) {
+            __syncwarp(mask);
         } else {
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(NT) : "memory");
         }

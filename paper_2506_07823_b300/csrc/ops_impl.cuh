@@ -236,11 +236,26 @@ static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
     }
 }
 
+// The one-chunk (sequential recursion) fused SQP of small SRBD states: the
+// row-per-lane kernel, two instances per one-warp CTA.
+template <int NX>
+static cudaError_t launch_sqp_rows(const SqpArgs& a, cudaStream_t st)
+{
+    constexpr size_t bytes = SqpRowsSmem<NX>::BYTES;
+    static std::atomic<uint64_t> smem_done{0};
+    if (cudaError_t e = ensure_smem(sqp_rows_kernel<NX>, bytes, smem_done); e != cudaSuccess)
+        return e;
+    sqp_rows_kernel<NX><<<(a.ka.count + 1) / 2, 32, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NX, int NU>
 static cudaError_t launch_sqp(const SqpArgs& a, int warps, cudaStream_t st)
 {
     switch (warps) {
-        case 1: return launch_sqp_w<NX, NU, 1>(a, st);
+        case 1:
+            if constexpr (NX == 12 && NU == 12) return launch_sqp_rows<NX>(a, st);
+            else return launch_sqp_w<NX, NU, 1>(a, st);
         case 4: return launch_sqp_w<NX, NU, 4>(a, st);
         case 8: return launch_sqp_w<NX, NU, 8>(a, st);
         case 16: return launch_sqp_w<NX, NU, 16>(a, st);
@@ -263,7 +278,9 @@ template <int NX, int NU>
 static size_t sqp_smem(int warps)
 {
     switch (warps) {
-        case 1: return sqp_smem_w<NX, NU, 1>();
+        case 1:
+            if constexpr (NX == 12 && NU == 12) return SqpRowsSmem<NX>::BYTES;
+            else return sqp_smem_w<NX, NU, 1>();
         case 4: return sqp_smem_w<NX, NU, 4>();
         case 8: return sqp_smem_w<NX, NU, 8>();
         case 16: return sqp_smem_w<NX, NU, 16>();

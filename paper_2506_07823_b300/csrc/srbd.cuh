@@ -63,6 +63,36 @@ __device__ __forceinline__ float barrier_delta(float xi, float dxa, float mu, fl
     return v1 - v0;
 }
 
+// The relaxed barrier split as B(z) = -mu ln max(z, delta) + q(z), where
+// q(z) = mu / (2 delta^2) (z - delta)(z - 3 delta) below delta and 0 above
+// (the same function as barrier3: at z < delta, -mu ln delta + q(z) is the
+// quadratic branch).  Branch-free forms of the value and slope, and of the
+// difference B(xi + dxa) - B(xi): the log part is -mu log1p((max(xn, delta)
+// - max(xi, delta)) / max(xi, delta)), whose argument is dxa itself when both
+// points lie above delta, and the quadratic parts are differenced as
+// mu / (2 delta^2) dxa (2 xi + dxa - 4 delta) when both lie below.
+__device__ __forceinline__ void barrier_vs(float xi, float mu, float delta, float& v, float& d1)
+{
+    const float m = fmaxf(xi, delta);
+    const float c = mu / (2.f * delta * delta);
+    const bool lo = xi < delta;
+    v = -mu * logf(m) + (lo ? c * (xi - delta) * (xi - 3.f * delta) : 0.f);
+    d1 = lo ? 2.f * c * (xi - 2.f * delta) : -mu / m;
+}
+
+__device__ __forceinline__ float barrier_diff(float xi, float dxa, float mu, float delta)
+{
+    const float xn = xi + dxa;
+    const float mi = fmaxf(xi, delta), mn = fmaxf(xn, delta);
+    const bool li = xi < delta, ln = xn < delta;
+    const float c = mu / (2.f * delta * delta);
+    const float dm = (!li && !ln) ? dxa : mn - mi;
+    const float lpart = -mu * log1pf(__fdividef(dm, mi));
+    const float qi = c * (xi - delta) * (xi - 3.f * delta), qn = c * (xn - delta) * (xn - 3.f * delta);
+    const float qpart = (li && ln) ? c * dxa * (2.f * xi + dxa - 4.f * delta) : (ln ? qn : 0.f) - (li ? qi : 0.f);
+    return lpart + qpart;
+}
+
 // friction-pyramid row c of a stance foot: xi = G_c . f
 __device__ __forceinline__ float cone_g(int c, int comp, float mu)
 {
@@ -287,13 +317,17 @@ struct SrbdSource {
         g.sync();
     }
     // Inputs of stage gs (x_k, x_{k+1}, lam_k, lam_{k+1}, xref_k, u_k, uref_k,
-    // contact_k) are first copied into the stage's IN area asynchronously.
+    // contact_k): fetch() issues their asynchronous copies into an input
+    // buffer (IN_FLOATS floats, 16-byte aligned) and commits them as one
+    // group; linearize() waits for the copies the thread issued, joins the
+    // group and linearises the stage from the buffer into st.  load() is the
+    // two back to back into the stage's own IN area.
+    template <int NX, int NU>
+    static constexpr int in_floats() { return 5 * round4(NX) + 2 * round4(NU) + round4(NX / 12 + 1); }
     template <int NX, int NU, int NT>
-    __device__ __forceinline__ void load(const Grp<NT>& g, float* st, int64_t gs, bool terminal) const
+    __device__ __forceinline__ void fetch(const Grp<NT>& g, float* in, int64_t gs, bool terminal) const
     {
-        using L = StageL<NX, NU>;
         constexpr int SX = round4(NX), SU = round4(NU);
-        float* in = st + L::IN;
         float* ix = in;
         float* ix1 = in + SX;
         float* il0 = in + 2 * SX;
@@ -319,9 +353,26 @@ struct SrbdSource {
             }
         }
         cp_async_commit();
-        cp_async_wait_all();
+    }
+    // PENDING: copy groups this thread committed after the one to consume
+    template <int NX, int NU, int NT, int PENDING = 0>
+    __device__ __forceinline__ void linearize(const Grp<NT>& g, float* st, const float* in,
+                                              bool terminal) const
+    {
+        constexpr int SX = round4(NX), SU = round4(NU);
+        cp_async_wait<PENDING>();
         g.sync();
-        srbd_linearize_stage<NX, NU, NT>(g, st, md, ix, iu, ix1, il0, il1, ixr, iur, ict, terminal);
+        const float* iu = in + 5 * SX;
+        srbd_linearize_stage<NX, NU, NT>(g, st, md, in, iu, in + SX, in + 2 * SX, in + 3 * SX,
+                                         in + 4 * SX, iu + SU,
+                                         reinterpret_cast<const uint8_t*>(iu + 2 * SU), terminal);
+    }
+    template <int NX, int NU, int NT>
+    __device__ __forceinline__ void load(const Grp<NT>& g, float* st, int64_t gs, bool terminal) const
+    {
+        float* in = st + StageL<NX, NU>::IN;
+        fetch<NX, NU, NT>(g, in, gs, terminal);
+        linearize<NX, NU, NT>(g, st, in, terminal);
     }
     __device__ __forceinline__ bool has_S() const { return false; }
 };

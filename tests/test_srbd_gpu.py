@@ -129,9 +129,11 @@ def run_oracle(prm, pr, iters, alpha_replay=None):
                            alpha_replay=alpha_replay)
 
 
-@pytest.mark.parametrize("warps", [4, 8, 16])
+@pytest.mark.parametrize("warps", [1, 4, 8, 16])
 @pytest.mark.parametrize("mode", ["replay", "free"])
 def test_sqp_parity(warps, mode):
+    """Fused SQP against the oracle; warps = 1 is the sequential recursion
+    with two instances per warp (here pairs of unequal horizons share one)."""
     from paper_2506_07823_b300 import pdilqr
     iters = 10
     insts, packed, Nv, off, x0 = srbd_case(4, 11, [25, 50, 75, 100])
@@ -310,3 +312,33 @@ def test_tensor_core_wait_timeout_status():
     torch.cuda.synchronize()
     assert info["status"].item() == 0
     assert rel(d["x"].double().cpu().numpy(), xr) <= REL_TOL
+
+
+def test_sqp_sequential_odd_batch():
+    """The two-instances-per-warp sequential solver on an odd batch (the last
+    warp runs one instance) with horizons 1 (degenerate) to 100, replaying
+    the oracle's step sizes."""
+    from paper_2506_07823_b300 import pdilqr
+    iters = 4
+    insts, packed, Nv, off, x0 = srbd_case(5, 91, [1, 100, 13, 2, 50])
+    prm = synth.srbd_params()
+    refs = [run_oracle(prm, pr, iters) for pr in insts]
+    d = dev(packed)
+    plan = pdilqr.Plan(12, 12, Nv, off, warps=1)
+    replay = torch.tensor(np.stack([r[3]["alpha"] for r in refs]).astype(np.float32), device="cuda")
+    info = plan.solve(pdilqr.srbd_model(prm), torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                      d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                      max_iters=iters, alpha_replay=replay)
+    torch.cuda.synchronize()
+    st = info["status"].cpu().numpy()
+    want = np.array([pdilqr.E_LINESEARCH if r[3]["status"] == 1 else 0 for r in refs])
+    assert np.array_equal(st, want), (st, want)
+    xs, us, ls = (d[k].double().cpu().numpy() for k in ("x", "u", "lam"))
+    for i, (xr, ur, lr, inf) in enumerate(refs):
+        if inf["status"] != 0:
+            continue
+        N, o = int(Nv[i]), int(off[i])
+        sl = slice(o, o + N + 1)
+        assert rel(xs[sl], xr) <= REL_TOL, (i, rel(xs[sl], xr))
+        assert rel(us[o:o + N], ur[:N]) <= REL_TOL, (i, rel(us[o:o + N], ur[:N]))
+        assert rel(ls[sl], lr) <= REL_TOL, (i, rel(ls[sl], lr))
