@@ -49,7 +49,7 @@ SEED = 0
 WORKLOAD = "srbd_batched_mpc"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sqp_kernel_traffic.json")
-KERNEL_SOURCES = ["dev_linalg.cuh", "kkt_scan.cuh", "srbd.cuh", "sqp.cuh"]
+KERNEL_SOURCES = ["dev_linalg.cuh", "kkt_scan.cuh", "srbd.cuh", "sqp.cuh", "sqp_rows.cuh"]
 
 def flops_per_stage(n: int, solver: str) -> float:
     """Algorithmic flops of one LQ KKT solve per stage for n = m: about 50 n^3
@@ -97,6 +97,11 @@ def executed_flops(n: int, m: int, N: int, chunks: int) -> float:
             if w > 0:
                 per += size * (build + comb)
     return per
+
+
+def kernel_name(W: int) -> str:
+    """The fused SQP kernel that runs the batch with W horizon chunks."""
+    return "sqp_rows_kernel<12>" if W == 1 else f"sqp_kernel<12,12,{W},1>"
 
 
 def kernel_source_hash() -> str:
@@ -417,7 +422,7 @@ def run_gpu(args):
         achieved = algo / (ms / 1e3) / 1e12
         traffic = None
         try:
-            tr = json.load(open(TRAFFIC_FILE)).get(f"sqp_kernel<12,12,{W},1>", {})
+            tr = json.load(open(TRAFFIC_FILE)).get(kernel_name(W), {})
             if tr.get("source_hash") == kernel_source_hash():
                 traffic = tr["bytes_per_launch_full"]
         except Exception:
@@ -476,7 +481,7 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ffma,
                          "unit": "TFLOP/s", "frac": achieved / peak_ffma,
                          "traffic": traffic,
-                         "kernel": f"sqp_kernel<12,12,{W},1>",
+                         "kernel": kernel_name(W),
                          "algorithmic_flops_per_step": algo,
                          "algorithmic_flops_per_stage": flops_per_stage(n, solver),
                          "executed_kkt_flops_per_step": executed,
