@@ -378,15 +378,15 @@ def run_gpu(args):
         plan.solve(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"],
                    work["uref"], work["contact"], max_iters=ITERS, info=info)
 
-    # the timed step replays a CUDA graph of the batched solve (one launch of
-    # the fused kernel); the trajectory reset and the L2 flush stay outside it
+    # the timed step replays the plan's captured CUDA graph of the batched
+    # solve (pdilqr_solve_capture: the counter reset and one launch of the
+    # fused kernel); the trajectory reset and the L2 flush stay outside it
     reset()
     solve_direct()
     torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        solve_direct()
-    solve = graph.replay
+    plan.capture(md, work["x0hat"], work["x"], work["u"], work["lam"], work["xref"],
+                 work["uref"], work["contact"], max_iters=ITERS, info=info)
+    solve = plan.replay
 
     for _ in range(args.warmup):
         reset()
@@ -431,6 +431,7 @@ def run_gpu(args):
         lqw = measure_lq_workloads(torch, pdilqr, dev, stream, args) if args.lq_workloads else None
         serving = None
         if args.serve_seconds > 0:
+            low = args.serve_rate_sustained
             serving = {
                 "workload": "Poisson arrivals, one real-time SQP iteration per request, N = 50, "
                             "256 clients: one robot (n = 12) or two robots (n = 24)",
@@ -438,10 +439,17 @@ def run_gpu(args):
                                                             args.serve_rate, 1024, 8, 2),
                 "one_request_per_launch_riccati": measure_serving(pdilqr, args, args.serve_seconds,
                                                                   args.serve_rate, 1, 1, 1),
+                "equal_load_note": f"both servers at {low:g} requests/s, a rate the one-request-"
+                                   "per-launch server sustains, so that its p99 is solve latency "
+                                   "and not queue growth",
+                "continuous_batching_scan_equal_load": measure_serving(
+                    pdilqr, args, args.serve_seconds, low, 1024, 8, 2),
+                "one_request_per_launch_riccati_equal_load": measure_serving(
+                    pdilqr, args, args.serve_seconds, low, 1, 1, 1),
                 "full_mix_workload": "Poisson arrivals, one real-time SQP iteration per request, "
                                      "N = 50, 1024 clients: 60 % one robot, 10 % each 2, 4, 8 "
                                      "and 16 robots (n = 12 R)",
-                "continuous_batching_full_mix": measure_serving(pdilqr, args, args.serve_seconds,
+                "continuous_batching_full_mix": measure_serving(pdilqr, args, args.mix_seconds,
                                                                 args.serve_rate, 1024, 8, 4,
                                                                 mix="full")}
         e2e = measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args)
@@ -468,7 +476,8 @@ def run_gpu(args):
                                   if W == 1 else f"parallel scan ({W} horizon chunks)"),
                        "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()},
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "cuda_graph": "the timed step replays a captured graph of the batched solve",
+                       "cuda_graph": "the timed step replays the plan's captured graph of the "
+                                     "batched solve (pdilqr_solve_capture / pdilqr_plan_replay)",
                        "parallelism": f"replicas{world}"},
             "latency_ms": {"batch_p50": pct(times, 50), "batch_p99": pct(times, 99),
                            **extras["latency"]},
@@ -985,6 +994,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="duration of each serving scenario (0 skips them)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (1/s)")
+    ap.add_argument("--serve-rate-sustained", type=float, default=400.0,
+                    help="the equal-load rate of both servers (one the one-request-per-launch "
+                         "server sustains)")
+    ap.add_argument("--mix-seconds", type=float, default=60.0,
+                    help="duration of the full robot-count mix (0 skips it with the others when "
+                         "--serve-seconds is 0)")
     ap.add_argument("--no-lq-workloads", dest="lq_workloads", action="store_false",
                     help="skip the whole-body LQ batch and single-LQR measurements")
     ap.add_argument("--sweep", action="store_true",

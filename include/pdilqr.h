@@ -286,6 +286,24 @@ PDILQR_API pdilqr_status pdilqr_solve(pdilqr_plan *plan, const pdilqr_srbd_model
                                       const float *uref, const uint8_t *contact,
                                       pdilqr_sqp_info *info, pdilqr_stream stream);
 
+/* Capture one pdilqr_solve with these arguments into a CUDA graph that the
+ * plan owns (replacing the plan's earlier graph, if any); pdilqr_plan_replay
+ * then launches it.  The graph holds the arguments' device pointers and the
+ * option values as they are now: a replay solves in place on the same
+ * arrays (x, u, lam are read as the warm start and overwritten, the info
+ * arrays rewritten), so the caller refills the inputs between replays.
+ * Nothing runs on the GPU during the capture.  The capture uses a private
+ * stream in relaxed mode; it may not be called while the calling thread
+ * captures another stream.  Errors: as pdilqr_solve, CUDA. */
+PDILQR_API pdilqr_status pdilqr_solve_capture(pdilqr_plan *plan, const pdilqr_srbd_model *model,
+                                              const pdilqr_sqp_opts *opts, const float *x0hat,
+                                              float *x, float *u, float *lam, const float *xref,
+                                              const float *uref, const uint8_t *contact,
+                                              pdilqr_sqp_info *info);
+/* Launch the plan's captured solve on `stream` (asynchronous).  Errors:
+ * INVALID_ARG (no graph captured), CUDA. */
+PDILQR_API pdilqr_status pdilqr_plan_replay(pdilqr_plan *plan, pdilqr_stream stream);
+
 /* ------------------------------------------------------------ serving loop */
 
 /* A continuous-batching MPC server (the real-time iteration of Sec. II-F: one
@@ -297,8 +315,11 @@ PDILQR_API pdilqr_status pdilqr_solve(pdilqr_plan *plan, const pdilqr_srbd_model
  * completes tickets as their batch finishes.  Warm-start trajectories,
  * multipliers and references stay resident on the device per client.
  * Admission: a client's state is carved from a device pool of
- * hbm_budget_bytes; when it does not fit the submit fails with
- * PDILQR_E_ADMISSION.  All waits are bounded. */
+ * hbm_budget_bytes, and the first client of a size class is admitted only if
+ * the device's free memory (cudaMemGetInfo) holds that class's batch
+ * workspace for every stream that may run it plus hbm_reserve_bytes; when
+ * either does not fit the submit fails with PDILQR_E_ADMISSION.  All waits
+ * are bounded. */
 typedef struct {
     int64_t hbm_budget_bytes;  /* device pool for client state (0: 1 GiB)         */
     int32_t max_batch;         /* requests per launch (0: 1024; 1: one per launch);
@@ -320,6 +341,8 @@ typedef struct {
                                /* the classes nrob = 1, 2, 4, 8, 16 (their nrob    */
                                /* fields are ignored; read during create only);    */
                                /* NULL: `model` for every class                    */
+    int64_t hbm_reserve_bytes; /* device memory left free when a size class's     */
+                               /* batch workspace is first needed (0: 256 MiB)    */
 } pdilqr_serve_opts;
 
 typedef struct {

@@ -8,7 +8,7 @@
 #include "kkt_scan.cuh"
 #include "residual.cuh"
 #include "sqp.cuh"
-#include "sqp_rows.cuh"
+#include "scan_rows.cuh"
 
 namespace pdl {
 

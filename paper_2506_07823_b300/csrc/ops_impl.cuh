@@ -249,16 +249,38 @@ static cudaError_t launch_sqp_rows(const SqpArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// The scan fused SQP of small SRBD states with row-per-lane chunks: one
+// instance per CTA, W chunks of 16 lanes (W / 2 warps).
+template <int NX, int W>
+static cudaError_t launch_sqp_scan_rows(const SqpArgs& a, cudaStream_t st)
+{
+    constexpr size_t bytes = ScanRowsSmem<NX, W>::BYTES;
+    static_assert(bytes <= kSmemMax, "scan work areas fit shared memory");
+    if (!a.lqcache) return cudaErrorInvalidValue;
+    static std::atomic<uint64_t> smem_done{0};
+    if (cudaError_t e = ensure_smem(sqp_scan_rows_kernel<NX, W>, bytes, smem_done); e != cudaSuccess)
+        return e;
+    sqp_scan_rows_kernel<NX, W><<<a.ka.count, 16 * W, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NX, int NU>
 static cudaError_t launch_sqp(const SqpArgs& a, int warps, cudaStream_t st)
 {
+    constexpr bool ROWS = NX == 12 && NU == 12;
     switch (warps) {
         case 1:
-            if constexpr (NX == 12 && NU == 12) return launch_sqp_rows<NX>(a, st);
+            if constexpr (ROWS) return launch_sqp_rows<NX>(a, st);
             else return launch_sqp_w<NX, NU, 1>(a, st);
-        case 4: return launch_sqp_w<NX, NU, 4>(a, st);
-        case 8: return launch_sqp_w<NX, NU, 8>(a, st);
-        case 16: return launch_sqp_w<NX, NU, 16>(a, st);
+        case 4:
+            if constexpr (ROWS) return launch_sqp_scan_rows<NX, 4>(a, st);
+            else return launch_sqp_w<NX, NU, 4>(a, st);
+        case 8:
+            if constexpr (ROWS) return launch_sqp_scan_rows<NX, 8>(a, st);
+            else return launch_sqp_w<NX, NU, 8>(a, st);
+        case 16:
+            if constexpr (ROWS) return launch_sqp_scan_rows<NX, 16>(a, st);
+            else return launch_sqp_w<NX, NU, 16>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -277,13 +299,20 @@ static size_t sqp_smem_w()
 template <int NX, int NU>
 static size_t sqp_smem(int warps)
 {
+    constexpr bool ROWS = NX == 12 && NU == 12;
     switch (warps) {
         case 1:
-            if constexpr (NX == 12 && NU == 12) return SqpRowsSmem<NX>::BYTES;
+            if constexpr (ROWS) return SqpRowsSmem<NX>::BYTES;
             else return sqp_smem_w<NX, NU, 1>();
-        case 4: return sqp_smem_w<NX, NU, 4>();
-        case 8: return sqp_smem_w<NX, NU, 8>();
-        case 16: return sqp_smem_w<NX, NU, 16>();
+        case 4:
+            if constexpr (ROWS) return ScanRowsSmem<NX, 4>::BYTES;
+            else return sqp_smem_w<NX, NU, 4>();
+        case 8:
+            if constexpr (ROWS) return ScanRowsSmem<NX, 8>::BYTES;
+            else return sqp_smem_w<NX, NU, 8>();
+        case 16:
+            if constexpr (ROWS) return ScanRowsSmem<NX, 16>::BYTES;
+            else return sqp_smem_w<NX, NU, 16>();
         default: return SIZE_MAX;
     }
 }

@@ -379,6 +379,47 @@ extern "C" pdilqr_status pdilqr_solve(pdilqr_plan* pl, const pdilqr_srbd_model* 
     return PDILQR_OK;
 }
 
+// ------------------------------------------------------ captured solves
+extern "C" pdilqr_status pdilqr_solve_capture(pdilqr_plan* pl, const pdilqr_srbd_model* md,
+                                              const pdilqr_sqp_opts* o, const float* x0hat,
+                                              float* x, float* u, float* lam, const float* xref,
+                                              const float* uref, const uint8_t* contact,
+                                              pdilqr_sqp_info* info)
+{
+    if (!pl) return PDILQR_E_INVALID_ARG;
+    cudaStream_t s = nullptr;
+    PD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return cuda_status(e);
+    }
+    const pdilqr_status st = pdilqr_solve(pl, md, o, x0hat, x, u, lam, xref, uref, contact, info,
+                                          (pdilqr_stream)s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);   // ends the capture whatever the solve returned
+    cudaStreamDestroy(s);
+    if (st != PDILQR_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (pl->graph) cudaGraphExecDestroy(pl->graph);
+    pl->graph = ex;
+    return PDILQR_OK;
+}
+
+extern "C" pdilqr_status pdilqr_plan_replay(pdilqr_plan* pl, pdilqr_stream stream)
+{
+    if (!pl || !pl->graph) return PDILQR_E_INVALID_ARG;
+    PD_CUDA(cudaGraphLaunch(pl->graph, (cudaStream_t)stream));
+    return PDILQR_OK;
+}
+
 // ------------------------------------------------ allocation-free scan solve
 // Scratch of pdilqr_kkt_scan_solve_noalloc: a file-scope device array that
 // every GPU loading this library holds until the process exits.  Host code

@@ -28,6 +28,7 @@ struct pdilqr_plan {
     float* lin_ws = nullptr;    // stage areas of the standalone linearisation (large sizes)
     int max_count = 0;   // capacity of the batch tables (capacity plans)
     int dbg = 0;         // test switches (PDILQR_DEBUG_*)
+    cudaGraphExec_t graph = nullptr;   // captured solve (pdilqr_solve_capture)
 
     template <typename T>
     cudaError_t alloc(T** ptr, size_t count_) {
@@ -40,6 +41,7 @@ struct pdilqr_plan {
         return e;
     }
     ~pdilqr_plan() {
+        if (graph) cudaGraphExecDestroy(graph);
         for (void* v : allocs) cudaFree(v);
     }
 };

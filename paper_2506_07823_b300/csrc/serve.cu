@@ -222,6 +222,7 @@ struct pdilqr_server {
     std::vector<Slot> slots;
     // statistics
     int64_t submitted = 0, completed = 0, refused = 0, batches = 0, batched_requests = 0;
+    bool class_admitted[5] = {false, false, false, false, false};   // free-memory check passed
     bool started = false;
     Clock::time_point t_first;
     std::vector<int64_t> lat;   // ring of recent latencies (ns)
@@ -289,6 +290,21 @@ int class_batch(const pdilqr_server* sv, int cls)
 // more than one stream they may hold all but one, which stays free for the
 // one- and two-robot classes.
 constexpr int kLargeClass = 2;
+
+// Device bytes of one stream's batch workspace for size class cls: the
+// capacity plan (policy, value function and closed-loop maps per stage slot,
+// the step buffers, the linearised-stage cache of the scan) and the staging
+// arrays ensure_res allocates.
+size_t class_res_bytes(const pdilqr_server* sv, int cls)
+{
+    const int nrob = 1 << cls;
+    const size_t n = 12 * (size_t)nrob, B = class_batch(sv, cls);
+    const size_t S = B * ((size_t)sv->opts.max_N + 1);
+    const SizeOps* ops = find_ops((int)n, (int)n);
+    const size_t lq = ops ? (size_t)ops->lq_stage_floats : 0;
+    const size_t per_slot = 3 * n * n + 6 * n + lq + 8 * n + 4 * nrob;
+    return sizeof(float) * S * per_slot + sizeof(float) * B * (n + 16);
+}
 
 pdilqr_status ensure_res(pdilqr_server* sv, Slot& sl, int cls)
 {
@@ -565,6 +581,7 @@ extern "C" pdilqr_status pdilqr_serve_create(const pdilqr_serve_opts* o, pdilqr_
     for (int c = 0; c < kClasses; ++c) sv->models[c] = o->class_models ? o->class_models[c] : o->model;
     sv->opts.class_models = nullptr;   // read here only
     if (sv->opts.hbm_budget_bytes <= 0) sv->opts.hbm_budget_bytes = int64_t(1) << 30;
+    if (sv->opts.hbm_reserve_bytes <= 0) sv->opts.hbm_reserve_bytes = int64_t(256) << 20;
     if (sv->opts.max_batch <= 0) sv->opts.max_batch = 1024;
     if (sv->opts.max_inflight <= 0) sv->opts.max_inflight = 2;
     if (sv->opts.max_N <= 0) sv->opts.max_N = 100;
@@ -632,6 +649,22 @@ extern "C" pdilqr_status pdilqr_serve_submit(pdilqr_server* sv, uint64_t client_
         c.n = n;
         c.N = q->N;
         c.bytes = client_bytes(q->nrob, q->N);
+        const int cls = class_of(q->nrob);
+        if (!sv->class_admitted[cls]) {
+            // the class's batch workspace is allocated when its first batch
+            // runs: admit its first client only if free memory holds it on
+            // every stream that may run the class, plus the reserve
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return PDILQR_E_CUDA;
+            const size_t streams = (size_t)(cls >= kLargeClass && sv->opts.max_inflight > 1
+                                                ? sv->opts.max_inflight - 1 : sv->opts.max_inflight);
+            const size_t need = class_res_bytes(sv, cls) * streams + (size_t)sv->opts.hbm_reserve_bytes;
+            if (free_b < need) {
+                sv->refused++;
+                return PDILQR_E_ADMISSION;
+            }
+            sv->class_admitted[cls] = true;
+        }
         if (!sv->pool.alloc(c.bytes, &c.off)) {
             sv->refused++;
             return PDILQR_E_ADMISSION;

@@ -63,11 +63,12 @@ struct RowRicL {
 // elimination without pivoting on the rows [G | H | h] (lane r: row r): for
 // an SPD G the pivots are the diagonal of its L D L^T factorisation, so
 // "every pivot positive and finite" is the SPD test.  Rows of K, k, P, p,
-// Abar, bbar are written to global memory at stage slot gs.  Returns false
-// (uniformly over the half) if G is not SPD.
+// Abar, bbar are written to global memory at stage slot gs (Abar, bbar also
+// to abar_sm when given: N rows, then N floats).  Returns false (uniformly
+// over the half) if G is not SPD.
 template <int N>
 __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, const KktArgs& a,
-                             int64_t gs, bool has_S)
+                             int64_t gs, bool has_S, float* abar_sm = nullptr)
 {
     using L = StageL<N, N>;
     using S = RowRicL<N>;
@@ -203,6 +204,10 @@ __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, cons
         st_row(Pt + r * N, pn);
         st_row(a.Abar + gs * N * N + r * N, ab);
         a.bbar[gs * N + r] = bb;
+        if (abar_sm) {             // also left in shared memory: rows, then bbar
+            st_row(abar_sm + r * N, ab);
+            abar_sm[N * N + r] = bb;
+        }
     }
     g.sync();
     // (f) P <- (P + P^T) / 2, the value function of the next step
@@ -286,8 +291,10 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, float v)
 
 // The line-search merit of merit_block ([0] J(0), [1] theta(0), [2] dphi,
 // [3 + t] J(a_t) - J(0), [13 + t] theta(a_t), [23] |dz|_inf, [25] |x|_inf)
-// for one single-robot instance (n = m = 12) by a 16-lane half, for the
-// step sizes a_t = 2^-t with T0 <= t <= T1 (and, when T0 = 0, the current
+// for one single-robot instance (n = m = 12) by a 16-lane half (stages
+// kfirst + lane, + kstep, ...: several halves may split an instance, each
+// writing its own sums to its `out`), for the step sizes a_t = 2^-t with
+// T0 <= t <= T1 (and, when T0 = 0, the current
 // point and the norms); slots of other step sizes are left untouched.
 // Every lane takes whole stages (k = lane, lane + 16, ...) and reads each
 // stage's data once: the tracking terms of J(a) - J(0) are the polynomial
@@ -304,7 +311,7 @@ template <int T0, int T1>
 __device__ void merit_rows(const Grp<16>& g, const pdilqr_srbd_model& md, const float* x,
                            const float* u, const float* dx, const float* du, const float* xr,
                            const float* ur, const uint8_t* ct, const float* x0hat, int N,
-                           float* acc, float* fbuf, double* out)
+                           float* acc, float* fbuf, double* out, int kfirst = 0, int kstep = 16)
 {
     constexpr int NS = 23;            // summed slots: out[0..22]
     constexpr int NT = T1 - T0 + 1;   // step sizes evaluated
@@ -313,7 +320,7 @@ __device__ void merit_rows(const Grp<16>& g, const pdilqr_srbd_model& md, const 
     for (int i = 0; i < 2 * NS; ++i) my[i] = 0.f;
     auto add = [&](int slot, float v) { acc2(my[2 * slot], my[2 * slot + 1], v); };
     float step = 0.f, xmax = 0.f;
-    for (int k = g.t; k <= N; k += 16) {
+    for (int k = kfirst + g.t; k <= N; k += kstep) {
         const bool term = k == N;
         const float* Wx = term ? md.WN : md.W;
         float A1 = 0.f, A2 = 0.f, J0 = 0.f, th0 = 0.f;
@@ -479,9 +486,84 @@ static __device__ __noinline__ void merit_rows_rest(const Grp<16>& g, const pdil
                                                     const float* x, const float* u, const float* dx,
                                                     const float* du, const float* xr, const float* ur,
                                                     const uint8_t* ct, const float* x0hat, int N,
-                                                    float* acc, float* fbuf, double* out)
+                                                    float* acc, float* fbuf, double* out,
+                                                    int kfirst = 0, int kstep = 16)
 {
-    merit_rows<1, 9>(g, md, x, u, dx, du, xr, ur, ct, x0hat, N, acc, fbuf, out);
+    merit_rows<1, 9>(g, md, x, u, dx, du, xr, ur, ct, x0hat, N, acc, fbuf, out, kfirst, kstep);
+}
+
+// Forward rollout of stages [k0, k1) of an instance at slot offset off with
+// horizon N, rows per lane: dx_{k+1} = Abar dx_k + bbar, du_k = K dx_k + k_k,
+// dlam_k = P dx_k + p_k (du_N = 0), from dx_{k0} (lane r < n holds its entry
+// r in xv0); the rows of K, P, Abar were written by the same lanes in the
+// backward sweep, and the rows of stage k + 1 are loaded while stage k is
+// applied.  xs: 16 floats of shared memory (the state broadcast).  Returns
+// false on a lane that wrote a non-finite value.
+template <int NX>
+__device__ bool rollout_rows(const Grp<16>& g, const KktArgs& ka, int64_t off, int N, int k0,
+                             int k1, float xv0, float* xs)
+{
+    constexpr int NU = NX;
+    const int r = g.t;
+    const bool row = r < NX;
+    float* dx = ka.dx + off * NX;
+    float* du = ka.du + off * NU;
+    float* dl = ka.dlam + off * NX;
+    float xv = xv0;
+    bool fin = true;
+    float Kc[NX], Pc[NX], Ac[NX], kc = 0.f, pc = 0.f, bc = 0.f;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) { Kc[j] = 0.f; Pc[j] = 0.f; Ac[j] = 0.f; }
+    if (row && k0 < k1) {
+        const int64_t gs = off + k0;
+        ld_row(Pc, ka.P + gs * NX * NX + r * NX);
+        pc = ka.p[gs * NX + r];
+        if (k0 < N) {
+            ld_row(Kc, ka.K + gs * NU * NX + r * NX);
+            ld_row(Ac, ka.Abar + gs * NX * NX + r * NX);
+            kc = ka.k[gs * NU + r];
+            bc = ka.bbar[gs * NX + r];
+        }
+    }
+    for (int k = k0; k < k1; ++k) {
+        const int64_t gs = off + k;
+        float Kn[NX], Pn[NX], An[NX], kn = 0.f, pn = 0.f, bn = 0.f;
+#pragma unroll
+        for (int j = 0; j < NX; ++j) { Kn[j] = 0.f; Pn[j] = 0.f; An[j] = 0.f; }
+        if (row && k + 1 < k1) {
+            ld_row(Pn, ka.P + (gs + 1) * NX * NX + r * NX);
+            pn = ka.p[(gs + 1) * NX + r];
+            if (k + 1 < N) {
+                ld_row(Kn, ka.K + (gs + 1) * NU * NX + r * NX);
+                ld_row(An, ka.Abar + (gs + 1) * NX * NX + r * NX);
+                kn = ka.k[(gs + 1) * NU + r];
+                bn = ka.bbar[(gs + 1) * NX + r];
+            }
+        }
+        if (row) xs[r] = xv;
+        g.sync();
+        if (row) {
+            float xl[NX];
+            ld_row(xl, xs);
+            float lv = pc, uv = kc, nv = bc;
+#pragma unroll
+            for (int j = 0; j < NX; ++j) {
+                lv = fmaf(Pc[j], xl[j], lv);
+                uv = fmaf(Kc[j], xl[j], uv);
+                nv = fmaf(Ac[j], xl[j], nv);
+            }
+            dx[(int64_t)k * NX + r] = xv;
+            dl[(int64_t)k * NX + r] = lv;
+            du[(int64_t)k * NU + r] = k < N ? uv : 0.f;
+            fin = fin && isfinite(xv) && isfinite(lv) && (k == N || isfinite(uv));
+            xv = nv;
+        }
+        g.sync();   // xs is rewritten at the next stage
+#pragma unroll
+        for (int j = 0; j < NX; ++j) { Pc[j] = Pn[j]; Kc[j] = Kn[j]; Ac[j] = An[j]; }
+        pc = pn; kc = kn; bc = bn;
+    }
+    return fin;
 }
 
 // ------------------------------------------------------------- the kernel
@@ -511,21 +593,14 @@ struct SqpRowsSmem {
 // bbar, du = K dx + k, dlam = P dx + p, the merit of the ten step sizes, the
 // filter decision of Sec. II-E and the update of Eq. (linear_rollout).
 template <int NX>
-__global__ void __launch_bounds__(32, 8) sqp_rows_kernel(const __grid_constant__ SqpArgs a)
+__device__ __forceinline__ void sqp_rows_instance(const SqpArgs& a, const Grp<16>& g, float* base,
+                                                  int inst)
 {
     using SM = SqpRowsSmem<NX>;
     using L = StageL<NX, NX>;
     constexpr int NU = NX;
-    extern __shared__ __align__(16) float smem[];
-    const int lane = threadIdx.x & 31, h = lane >> 4;
-    const int slot = 2 * blockIdx.x + h;
-    if (slot >= a.ka.count) return;   // an odd count: the other half runs alone
-    const int inst = a.ka.order ? a.ka.order[slot] : slot;
-    Grp<16> g{lane & 15, 0};
-    g.mask = 0xffffu << (16 * h);
     const int r = g.t;
     const bool row = r < NX;
-    float* base = smem + h * SM::PER;
     float* st = base + SM::ST;
     float* scr = base + SM::SCR;
     float* xs = base + SM::XS;
@@ -581,63 +656,8 @@ __global__ void __launch_bounds__(32, 8) sqp_rows_kernel(const __grid_constant__
             status = ST_NOT_SPD;
             break;
         }
-        // ---- forward rollout from dx_0 = xhat_0 - x_0: dx_{k+1} = Abar dx_k + bbar,
-        // du = K dx + k, dlam = P dx + p, one row per lane (the rows were
-        // written by the same lane in the backward sweep); the rows of stage
-        // k + 1 are loaded while stage k is applied
-        float xv = row ? xh[r] - x[r] : 0.f;
-        bool fin = true;
-        float Kc[NX], Pc[NX], Ac[NX], kc = 0.f, pc = 0.f, bc = 0.f;
-#pragma unroll
-        for (int j = 0; j < NX; ++j) { Kc[j] = 0.f; Pc[j] = 0.f; Ac[j] = 0.f; }
-        if (row) {
-            ld_row(Pc, ka.P + off * NX * NX + r * NX);
-            pc = ka.p[off * NX + r];
-            if (N > 0) {
-                ld_row(Kc, ka.K + off * NU * NX + r * NX);
-                ld_row(Ac, ka.Abar + off * NX * NX + r * NX);
-                kc = ka.k[off * NU + r];
-                bc = ka.bbar[off * NX + r];
-            }
-        }
-        for (int k = 0; k <= N; ++k) {
-            const int64_t gs = off + k;
-            float Kn[NX], Pn[NX], An[NX], kn = 0.f, pn = 0.f, bn = 0.f;
-#pragma unroll
-            for (int j = 0; j < NX; ++j) { Kn[j] = 0.f; Pn[j] = 0.f; An[j] = 0.f; }
-            if (row && k < N) {
-                ld_row(Pn, ka.P + (gs + 1) * NX * NX + r * NX);
-                pn = ka.p[(gs + 1) * NX + r];
-                if (k + 1 < N) {
-                    ld_row(Kn, ka.K + (gs + 1) * NU * NX + r * NX);
-                    ld_row(An, ka.Abar + (gs + 1) * NX * NX + r * NX);
-                    kn = ka.k[(gs + 1) * NU + r];
-                    bn = ka.bbar[(gs + 1) * NX + r];
-                }
-            }
-            if (row) xs[r] = xv;
-            g.sync();
-            if (row) {
-                float xl[NX];
-                ld_row(xl, xs);
-                float lv = pc, uv = kc, nv = bc;
-#pragma unroll
-                for (int j = 0; j < NX; ++j) {
-                    lv = fmaf(Pc[j], xl[j], lv);
-                    uv = fmaf(Kc[j], xl[j], uv);
-                    nv = fmaf(Ac[j], xl[j], nv);
-                }
-                dx[(int64_t)k * NX + r] = xv;
-                dl[(int64_t)k * NX + r] = lv;
-                du[(int64_t)k * NU + r] = k < N ? uv : 0.f;
-                fin = fin && isfinite(xv) && isfinite(lv) && (k == N || isfinite(uv));
-                xv = nv;
-            }
-            g.sync();   // xs is rewritten at the next stage
-#pragma unroll
-            for (int j = 0; j < NX; ++j) { Pc[j] = Pn[j]; Kc[j] = Kn[j]; Ac[j] = An[j]; }
-            pc = pn; kc = kn; bc = bn;
-        }
+        // ---- forward rollout from dx_0 = xhat_0 - x_0
+        const bool fin = rollout_rows<NX>(g, ka, off, N, 0, N + 1, row ? xh[r] - x[r] : 0.f, xs);
         if (__any_sync(g.mask, !fin)) {
             status = ST_NONFINITE;
             break;
@@ -731,6 +751,26 @@ __global__ void __launch_bounds__(32, 8) sqp_rows_kernel(const __grid_constant__
         if (a.alpha)
             for (int it = iters; it < a.max_iters; ++it) a.alpha[(int64_t)inst * a.max_iters + it] = 0.f;
     }
+}
+
+
+// CTAs of one warp, two instances (consecutive entries of the longest-first
+// order) per warp.  (A persistent form, a grid of the resident CTAs pulling
+// pairs from a counter, measured the same on the 4096-instance batch and 4 %
+// slower on one instance, its loop doubling the register spills; the
+// hardware's CTA scheduling over the longest-first order already balances
+// the batch, whose 2048 CTAs fit in 1.7 waves.)
+template <int NX>
+__global__ void __launch_bounds__(32, 8) sqp_rows_kernel(const __grid_constant__ SqpArgs a)
+{
+    using SM = SqpRowsSmem<NX>;
+    extern __shared__ __align__(16) float smem[];
+    const int lane = threadIdx.x & 31, h = lane >> 4;
+    const int slot = 2 * blockIdx.x + h;
+    if (slot >= a.ka.count) return;   // an odd count: the other half runs alone
+    Grp<16> g{lane & 15, 0};
+    g.mask = 0xffffu << (16 * h);
+    sqp_rows_instance<NX>(a, g, smem + h * SM::PER, a.ka.order ? a.ka.order[slot] : slot);
 }
 
 }  // namespace pdl

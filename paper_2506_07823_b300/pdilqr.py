@@ -122,6 +122,9 @@ _lib.pdilqr_merit_eval.argtypes = [_vp, ctypes.POINTER(SrbdModel), ctypes.POINTE
                                    _vp, _vp, _vp, _vp, _vp]
 _lib.pdilqr_solve.argtypes = [_vp, ctypes.POINTER(SrbdModel), ctypes.POINTER(_SqpOpts),
                               _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_SqpInfo), _vp]
+_lib.pdilqr_solve_capture.argtypes = [_vp, ctypes.POINTER(SrbdModel), ctypes.POINTER(_SqpOpts),
+                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_SqpInfo)]
+_lib.pdilqr_plan_replay.argtypes = [_vp, _vp]
 
 
 _lib.pdilqr_kkt_scan_solve_noalloc.argtypes = [
@@ -313,8 +316,9 @@ class Plan:
 
     def solve(self, model: SrbdModel, x0hat, x, u, lam, xref, uref, contact, max_iters=10,
               tol_step=0.0, tol_theta=0.0, c_armijo=1e-4, theta_frac=1e-2, alpha_replay=None,
-              info: dict | None = None, stream=None) -> dict:
-        """Run the fused SQP in place on (x, u, lam); returns the info tensors."""
+              info: dict | None = None, stream=None, capture: bool = False) -> dict:
+        """Run the fused SQP in place on (x, u, lam); returns the info tensors.
+        With ``capture`` the solve is captured into the plan's graph instead."""
         dev = x.device
         if info is None:
             info = {"iters": torch.zeros(self.count, device=dev, dtype=torch.int32),
@@ -329,12 +333,26 @@ class Plan:
                        _ptr(info.get("alpha"), name="alpha"),
                        _ptr(info.get("J"), torch.float64, "J"),
                        _ptr(info.get("theta"), torch.float64, "theta"))
-        _check(_lib.pdilqr_solve(self._h, ctypes.byref(model), ctypes.byref(o),
-                                 _ptr(x0hat, name="x0hat"), _ptr(x, name="x"), _ptr(u, name="u"),
-                                 _ptr(lam, name="lam"), _ptr(xref, name="xref"),
-                                 _ptr(uref, name="uref"), _ptr(contact, torch.uint8, "contact"),
-                                 ctypes.byref(inf), _stream(stream)), "pdilqr_solve")
+        args = (_ptr(x0hat, name="x0hat"), _ptr(x, name="x"), _ptr(u, name="u"),
+                _ptr(lam, name="lam"), _ptr(xref, name="xref"), _ptr(uref, name="uref"),
+                _ptr(contact, torch.uint8, "contact"), ctypes.byref(inf))
+        if capture:
+            _check(_lib.pdilqr_solve_capture(self._h, ctypes.byref(model), ctypes.byref(o), *args),
+                   "pdilqr_solve_capture")
+        else:
+            _check(_lib.pdilqr_solve(self._h, ctypes.byref(model), ctypes.byref(o), *args,
+                                     _stream(stream)), "pdilqr_solve")
         return info
+
+    def capture(self, *args, **kw) -> dict:
+        """Capture ``solve`` with these arguments into the plan's CUDA graph
+        (pdilqr_solve_capture; nothing runs); ``replay`` launches it."""
+        kw.pop("stream", None)
+        return self.solve(*args, capture=True, **kw)
+
+    def replay(self, stream=None):
+        """Launch the plan's captured solve (pdilqr_plan_replay)."""
+        _check(_lib.pdilqr_plan_replay(self._h, _stream(stream)), "pdilqr_plan_replay")
 
 
 # ------------------------------------------------------------------ serving
@@ -343,7 +361,7 @@ class _ServeOpts(ctypes.Structure):
                 ("max_inflight", ctypes.c_int32), ("max_N", ctypes.c_int32),
                 ("sqp_iters", ctypes.c_int32), ("warps", ctypes.c_int32),
                 ("batch_window_us", ctypes.c_int32), ("model", SrbdModel),
-                ("class_models", ctypes.POINTER(SrbdModel))]
+                ("class_models", ctypes.POINTER(SrbdModel)), ("hbm_reserve_bytes", ctypes.c_int64)]
 
 SERVE_NROB = (1, 2, 4, 8, 16)   # the server's size classes (robots per client)
 
@@ -389,17 +407,20 @@ class Server:
 
     def __init__(self, model_params: dict, hbm_budget_bytes: int = 1 << 30, max_batch: int = 1024,
                  max_inflight: int = 2, max_N: int = 100, sqp_iters: int = 1, warps: int = 8,
-                 batch_window_us: int = 0, class_params: dict | None = None):
+                 batch_window_us: int = 0, class_params: dict | None = None,
+                 hbm_reserve_bytes: int = 0):
         """``class_params`` optionally maps a robot count (1, 2, 4, 8, 16) to the
         model constants of that class (formation offsets differ per count);
-        classes it does not name use ``model_params``."""
+        classes it does not name use ``model_params``.  ``hbm_reserve_bytes``:
+        device memory the free-memory admission check keeps free (0: 256 MiB)."""
         cm = None
         if class_params is not None:
             cm = (SrbdModel * len(SERVE_NROB))(
                 *[srbd_model(class_params.get(r, model_params)) for r in SERVE_NROB])
         o = _ServeOpts(int(hbm_budget_bytes), int(max_batch), int(max_inflight), int(max_N),
                        int(sqp_iters), int(warps), int(batch_window_us), srbd_model(model_params),
-                       ctypes.cast(cm, ctypes.POINTER(SrbdModel)) if cm is not None else None)
+                       ctypes.cast(cm, ctypes.POINTER(SrbdModel)) if cm is not None else None,
+                       int(hbm_reserve_bytes))
         h = _vp()
         _check(_lib.pdilqr_serve_create(ctypes.byref(o), ctypes.byref(h)), "pdilqr_serve_create")
         self._h = h

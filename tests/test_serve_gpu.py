@@ -133,6 +133,26 @@ def test_admission_refused_then_released():
     srv.close()
 
 
+def test_admission_by_free_device_memory():
+    """The first client of a size class is admitted only if the device's free
+    memory holds the class's batch workspace plus the reserve: with a reserve
+    larger than any device the client is refused before anything is
+    allocated; with the default reserve the same client is admitted."""
+    from paper_2506_07823_b300 import pdilqr
+    prm = synth.srbd_params()
+    srv = pdilqr.Server(prm, hbm_budget_bytes=64 << 20, max_N=50, hbm_reserve_bytes=1 << 60)
+    pr = problem(3)
+    with pytest.raises(pdilqr.PdilqrError) as e:
+        submit(srv, 3, pr, 0)
+    assert e.value.code == pdilqr.E_ADMISSION
+    assert srv.stats()["refused"] == 1
+    srv.close()
+    srv = pdilqr.Server(prm, hbm_budget_bytes=64 << 20, max_N=50)   # default reserve
+    srv.poll(submit(srv, 3, pr, 0))
+    assert srv.stats()["refused"] == 0
+    srv.close()
+
+
 def test_snapshot_restore_resumes():
     pr = problem(9)
     srv = make_server()

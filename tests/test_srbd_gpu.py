@@ -342,3 +342,35 @@ def test_sqp_sequential_odd_batch():
         assert rel(xs[sl], xr) <= REL_TOL, (i, rel(xs[sl], xr))
         assert rel(us[o:o + N], ur[:N]) <= REL_TOL, (i, rel(us[o:o + N], ur[:N]))
         assert rel(ls[sl], lr) <= REL_TOL, (i, rel(ls[sl], lr))
+
+
+def test_captured_solve_replays_like_a_direct_solve():
+    """The plan's own CUDA graph (pdilqr_solve_capture / pdilqr_plan_replay)
+    reproduces a direct solve bit for bit, replay after replay, for both the
+    sequential and the scan solver."""
+    from paper_2506_07823_b300 import pdilqr
+    insts, packed, Nv, off, x0 = srbd_case(5, 31, [25, 50, 75, 100, 3])
+    prm = synth.srbd_params()
+    md = pdilqr.srbd_model(prm)
+    x0d = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    for warps in (1, 8):
+        ref = dev(packed)
+        plan = pdilqr.Plan(12, 12, Nv, off, warps=warps)
+        want = plan.solve(md, x0d, ref["x"], ref["u"], ref["lam"], ref["xref"], ref["uref"],
+                          ref["contact"], max_iters=4)
+        torch.cuda.synchronize()
+        d = dev(packed)
+        base = {k: v.clone() for k, v in d.items()}
+        info = plan.capture(md, x0d, d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                            max_iters=4)
+        torch.cuda.synchronize()
+        assert torch.equal(d["x"], base["x"])          # the capture ran nothing
+        for _ in range(2):
+            for k in ("x", "u", "lam"):
+                d[k].copy_(base[k])
+            plan.replay()
+            torch.cuda.synchronize()
+            for k in ("x", "u", "lam"):
+                assert torch.equal(d[k], ref[k]), (warps, k)
+            assert torch.equal(info["status"], want["status"])
+            assert torch.equal(info["iters"], want["iters"])
