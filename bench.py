@@ -101,7 +101,7 @@ def executed_flops(n: int, m: int, N: int, chunks: int) -> float:
 
 def kernel_name(W: int) -> str:
     """The fused SQP kernel that runs the batch with W horizon chunks."""
-    return "sqp_rows_kernel<12>" if W == 1 else f"sqp_kernel<12,12,{W},1>"
+    return "sqp_rows_kernel<12>" if W == 1 else f"sqp_scan_rows_kernel<12,{W}>"
 
 
 def kernel_source_hash() -> str:
@@ -453,6 +453,7 @@ def run_gpu(args):
                                                                 args.serve_rate, 1024, 8, 4,
                                                                 mix="full")}
         e2e = measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args)
+        sweep = measure_sweep(torch, pdilqr, dev, stream, args.sweep_reps) if args.sweep_reps > 0 else None
         cpu = None
         vs_oracle = None
         if pool is not None:
@@ -484,6 +485,7 @@ def run_gpu(args):
             "comparators": extras["comparators"],
             "serving": serving,
             "lq_workloads": lqw,
+            "sweep": sweep,
             "status_counts": {str(int(s)): int((st == s).sum()) for s in np.unique(st)},
             "vs_oracle": vs_oracle,
             "kkt_solves_per_step": kkt_all,
@@ -874,8 +876,11 @@ def run_sweep(args):
     from paper_2506_07823_b300 import pdilqr
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
-    reps = args.latency_reps
+    return measure_sweep(torch, pdilqr, dev, torch.cuda.current_stream(), args.latency_reps)
+
+
+def measure_sweep(torch, pdilqr, dev, stream, reps):
+    """The sweep of ``run_sweep`` with ``reps`` graph replays per point."""
 
     def latency(nrob, N, warps):
         prm = synth.srbd_params(nrob)
@@ -1002,6 +1007,9 @@ def main():
                          "--serve-seconds is 0)")
     ap.add_argument("--no-lq-workloads", dest="lq_workloads", action="store_false",
                     help="skip the whole-body LQ batch and single-LQR measurements")
+    ap.add_argument("--sweep-reps", type=int, default=20,
+                    help="graph replays per point of the horizon / robot-count sweep that the "
+                         "bench line carries (0: leave it out)")
     ap.add_argument("--sweep", action="store_true",
                     help="print the horizon / robot-count latency sweep instead of the bench line")
     ap.add_argument("--peaks", action="store_true",

@@ -144,7 +144,12 @@ PDILQR_API pdilqr_status pdilqr_kkt_scan_solve(pdilqr_plan *plan, const pdilqr_l
                                     pdilqr_kkt_out *out, pdilqr_stream stream);
 
 /* The same system by the sequential Riccati recursion and forward rollout of
- * Sec. II-C (the comparator), one warp per instance; honours opts.refine. */
+ * Sec. II-C (the comparator): one warp per instance for n <= 12, one CTA of
+ * 128 threads per instance for (n, m) = (24, 24) and (36, 24), with the
+ * larger sizes again one warp per instance; honours opts.refine.  Status per
+ * instance as for pdilqr_kkt_scan_solve (E_NOT_SPD when a pivot of some
+ * G_k = R_k + B_k^T P_k+1 B_k is not positive, E_NONFINITE when an output is
+ * not finite). */
 PDILQR_API pdilqr_status pdilqr_riccati_solve(pdilqr_plan *plan, const pdilqr_lq *lq, const float *s,
                                    pdilqr_kkt_out *out, pdilqr_stream stream);
 

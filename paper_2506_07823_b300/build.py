@@ -22,13 +22,6 @@ def _inputs():
     return files
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(f) > t for f in _inputs())
-
-
 def _compile(nvcc, src, obj, verbose):
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fvisibility=hidden", "-I" + INCLUDE, "-c", "-o", obj, src]
@@ -39,16 +32,27 @@ def _compile(nvcc, src, obj, verbose):
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit (in parallel) and link libpdilqr.so."""
-    if not force and not stale():
-        return LIB
+    """Compile the translation units that are out of date (in parallel) and
+    link libpdilqr.so.  A unit is recompiled when its object is older than the
+    unit itself or than any header (headers are shared by every unit)."""
     from concurrent.futures import ThreadPoolExecutor
     nvcc = os.environ.get("NVCC", "nvcc")
     os.makedirs(BUILD_DIR, exist_ok=True)
     jobs = [(os.path.join(CSRC, src), os.path.join(BUILD_DIR, src.replace(".cu", ".o")))
             for src in SOURCES]
-    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
-        objs = list(ex.map(lambda j: _compile(nvcc, j[0], j[1], verbose), jobs))
+    headers = max(os.path.getmtime(f) for f in _inputs() if not f.endswith(".cu"))
+
+    def fresh(src, obj):
+        return (not force and os.path.exists(obj) and
+                os.path.getmtime(obj) >= max(os.path.getmtime(src), headers))
+
+    todo = [j for j in jobs if not fresh(*j)]
+    objs = [j[1] for j in jobs]
+    if not todo and os.path.exists(LIB) and \
+            os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
+        return LIB
+    with ThreadPoolExecutor(max_workers=max(1, len(todo))) as ex:
+        list(ex.map(lambda j: _compile(nvcc, j[0], j[1], verbose), todo))
     tmp = LIB + ".tmp%d" % os.getpid()
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
     os.replace(tmp, LIB)

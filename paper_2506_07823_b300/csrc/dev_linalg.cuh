@@ -154,17 +154,22 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 }
 
 // Poll phase `phase` of an mbarrier until it completes or limit_ns pass (also
-// capped in polls); returns whether it completed.
+// capped in polls); returns whether it completed.  The clock is first read
+// after 64 polls, so that a wait that completes at once costs no timer read.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase, uint64_t limit_ns)
 {
-    const uint64_t t0 = globaltimer_ns();
+    uint64_t t0 = 0;
     for (uint32_t it = 0; it < (1u << 28); ++it) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done) : "r"((uint32_t)__cvta_generic_to_shared(mbar)), "r"(phase) : "memory");
         if (done) return true;
-        if ((it & 63) == 63 && globaltimer_ns() - t0 > limit_ns) return false;
+        if ((it & 63) == 63) {
+            const uint64_t now = globaltimer_ns();
+            if (it == 63) t0 = now;
+            else if (now - t0 > limit_ns) return false;
+        }
     }
     return false;
 }
@@ -457,15 +462,20 @@ __device__ void mm_tc(const Grp<NT>& g, float* out, int ldo, const float* A, int
         if (!failed) {
             const bool done = mbar_wait_bounded(&cx->mbar, phase, kTcWaitNs);
             // one verdict for the whole CTA (the group is the CTA), so that
-            // the TMEM loads below run on all warps or on none
+            // the TMEM loads below run on all warps or on none; the barrier
+            // also orders the next chunk's staging after every thread's wait
             failed = __syncthreads_or(done ? 0 : 1) != 0;
-            // MMAs possibly still in flight get a second bounded wait before
-            // their operands and accumulators are given up
-            if (failed && !done) mbar_wait_bounded(&cx->mbar, phase, kTcDrainNs);
             phase ^= 1;
+            if (failed) {
+                // MMAs possibly still in flight get a second bounded wait
+                // before their operands and accumulators are given up
+                if (!done) mbar_wait_bounded(&cx->mbar, phase ^ 1, kTcDrainNs);
+                g.sync();
+            }
+        } else {
+            g.sync();
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        g.sync();
         if (failed) break;   // uniform: no further chunk is staged or issued
     }
     // read the accumulators back: out = D + sgn * acc.  A lane holds one row

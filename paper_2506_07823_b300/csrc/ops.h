@@ -9,6 +9,7 @@
 #include "residual.cuh"
 #include "sqp.cuh"
 #include "scan_rows.cuh"
+#include "riccati_cta.cuh"
 
 namespace pdl {
 

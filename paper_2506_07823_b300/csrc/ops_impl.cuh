@@ -134,32 +134,60 @@ static cudaError_t launch_scan(const KktArgs& a, int warps, cudaStream_t st)
     }
 }
 
+// Sizes whose sequential recursion runs one 128-thread CTA per instance
+// (register-tiled products, column-per-thread elimination); the others run
+// one warp per instance.
+template <int NX, int NU>
+struct UseRicCta {
+    static constexpr bool value = NX >= 24 && NX + NU + 1 <= 64 && NX % 6 == 0 && NU % 8 == 0;
+};
+
 template <int NX, int NU>
 static cudaError_t launch_riccati(const KktArgs& a, cudaStream_t st)
 {
-    using SM = RicSmem<NX, NU>;
-    // warps (instances) per block: up to 4, as many as fit in shared memory
-    constexpr int FIT = (int)((227 * 1024) / SM::BYTES);
-    constexpr int WPB = FIT >= 4 ? 4 : (FIT >= 1 ? FIT : 1);
-    constexpr size_t bytes = SM::BYTES * WPB;
-    if constexpr (bytes > kSmemMax) {
-        return cudaErrorInvalidConfiguration;
+    if constexpr (UseRicCta<NX, NU>::value) {
+        constexpr size_t bytes = RicCtaL<NX, NU>::BYTES;
+        static std::atomic<uint64_t> smem_done{0};
+        if (cudaError_t e = ensure_smem(riccati_cta_kernel<NX, NU>, bytes, smem_done); e != cudaSuccess)
+            return e;
+        riccati_cta_kernel<NX, NU><<<a.count, kRcThreads, bytes, st>>>(a);
+        return cudaGetLastError();
     } else {
-    static std::atomic<uint64_t> smem_done{0};
-    if (cudaError_t e = ensure_smem(riccati_kernel<NX, NU>, bytes, smem_done); e != cudaSuccess)
-        return e;
-    const int grid = (a.count + WPB - 1) / WPB;
-    riccati_kernel<NX, NU><<<grid, 32 * WPB, bytes, st>>>(a);
-    return cudaGetLastError();
+        using SM = RicSmem<NX, NU>;
+        // warps (instances) per block: up to 4, as many as fit in shared memory
+        constexpr int FIT = (int)((227 * 1024) / SM::BYTES);
+        constexpr int WPB = FIT >= 4 ? 4 : (FIT >= 1 ? FIT : 1);
+        constexpr size_t bytes = SM::BYTES * WPB;
+        if constexpr (bytes > kSmemMax) {
+            return cudaErrorInvalidConfiguration;
+        } else {
+            static std::atomic<uint64_t> smem_done{0};
+            if (cudaError_t e = ensure_smem(riccati_kernel<NX, NU>, bytes, smem_done); e != cudaSuccess)
+                return e;
+            const int grid = (a.count + WPB - 1) / WPB;
+            riccati_kernel<NX, NU><<<grid, 32 * WPB, bytes, st>>>(a);
+            return cudaGetLastError();
+        }
     }
 }
 
 template <int NX, int NU>
 static cudaError_t launch_resid(const ResidArgs& a, cudaStream_t st)
 {
-    const int64_t blocks = (a.total_stages + 7) / 8;
-    kkt_residual_kernel<NX, NU><<<(unsigned)blocks, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    if constexpr (ResSmemCfg<NX, NU>::value && NX % 4 == 0 && NU % 4 == 0) {
+        using C = ResSmemCfg<NX, NU>;
+        static std::atomic<uint64_t> smem_done{0};
+        if (cudaError_t e = ensure_smem(kkt_residual_smem_kernel<NX, NU>, C::BYTES, smem_done);
+            e != cudaSuccess)
+            return e;
+        const int64_t blocks = (a.total_stages + C::SPB - 1) / C::SPB;
+        kkt_residual_smem_kernel<NX, NU><<<(unsigned)blocks, C::THREADS, C::BYTES, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        const int64_t blocks = (a.total_stages + 7) / 8;
+        kkt_residual_kernel<NX, NU><<<(unsigned)blocks, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
 }
 
 // Stage slots per block of the standalone linearisation and where its stage

@@ -190,9 +190,15 @@ static KktArgs make_args(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s, f
     return a;
 }
 
+// Every per-stage array is read (and the policy outputs written) with 16-byte
+// accesses: a misaligned pointer is an invalid argument, not a fault.
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 static bool lq_ok(const pdilqr_lq* lq)
 {
-    return lq && lq->A && lq->B && lq->c && lq->Q && lq->R && lq->q && lq->r;
+    return lq && lq->A && lq->B && lq->c && lq->Q && lq->R && lq->q && lq->r &&
+           aligned16(lq->A) && aligned16(lq->B) && aligned16(lq->c) && aligned16(lq->Q) &&
+           aligned16(lq->R) && aligned16(lq->q) && aligned16(lq->r) && aligned16(lq->S);
 }
 
 static pdilqr_status residual_into(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s,
@@ -235,6 +241,8 @@ static pdilqr_status solve_common(pdilqr_plan* pl, const pdilqr_lq* lq, const fl
                                   pdilqr_kkt_out* out, cudaStream_t st, bool scan)
 {
     if (!pl || !lq_ok(lq) || !s || !out || !out->dx || !out->du || !out->dlam || !out->status)
+        return PDILQR_E_INVALID_ARG;
+    if (!aligned16(out->K) || !aligned16(out->k) || !aligned16(out->P) || !aligned16(out->p))
         return PDILQR_E_INVALID_ARG;
     if (scan && pl->ops->scan_smem(pl->warps) > kSmemMax && !pl->gws) return PDILQR_E_INVALID_ARG;
     auto run = [&](const KktArgs& a) -> cudaError_t {

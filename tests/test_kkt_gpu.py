@@ -112,11 +112,14 @@ def test_ltv_parity_ragged(solver, warps, n, m):
 
 
 @pytest.mark.parametrize("solver", ["scan", "riccati"])
-def test_cross_term_S(solver):
-    n, m = 4, 2
-    insts, packed, Nv, off, s = make_batch(n, m, [7, 30, 64], seed=5, with_S=True)
+@pytest.mark.parametrize("n,m", [(4, 2), (24, 24), (36, 24)])
+def test_cross_term_S(solver, n, m):
+    """A nonzero cross term S (m x n) through every path that reads it (the
+    one-CTA recursion of n = 24 and 36 adds S in H and S^T [K | k] in the
+    value function)."""
+    insts, packed, Nv, off, s = make_batch(n, m, [7, 30, 64], seed=5 + n, with_S=True)
     from paper_2506_07823_b300.pdilqr import Plan
-    plan = Plan(n, m, Nv, off, warps=8)
+    plan = Plan(n, m, Nv, off, warps=8 if n == 4 else 4)
     lq, sd = to_dev(packed, s, True)
     fn = plan.kkt_scan_solve if solver == "scan" else plan.riccati_solve
     out = fn(lq, sd)
@@ -179,13 +182,18 @@ def test_whole_body_sized_workload(solver):
     assert float(backward_error(out["resid"]).max()) <= BWD_TOL
 
 
-def test_residual_kernel_matches_oracle():
-    """The FP64 residual kernel reproduces the oracle's residual norms."""
-    n, m = 4, 2
-    insts, packed, Nv, off, s = make_batch(n, m, [3, 9], seed=3)
+@pytest.mark.parametrize("n,m,with_S", [(4, 2, False), (12, 12, False), (24, 24, True),
+                                          (36, 24, False), (36, 24, True)])
+def test_residual_kernel_matches_oracle(n, m, with_S):
+    """The FP64 residual kernels (one warp per stage slot at n = 4; the
+    shared-memory staged form with one thread per row at n = 12, 24, 36)
+    reproduce the oracle's residual norms, with and without S, over a batch
+    whose slots do not fill the last block."""
+    Ns = [3, 9] if n == 4 else [3, 9, 1, 6]
+    insts, packed, Nv, off, s = make_batch(n, m, Ns, seed=3 + n, with_S=with_S)
     from paper_2506_07823_b300.pdilqr import Plan
     plan = Plan(n, m, Nv, off)
-    lq, sd = to_dev(packed, s, False)
+    lq, sd = to_dev(packed, s, with_S)
     g = np.random.default_rng(0)
     T = plan.total
     z = [g.normal(0, 1, (T, n)).astype(np.float32), g.normal(0, 1, (T, m)).astype(np.float32),
