@@ -692,26 +692,40 @@ def measure_lq_workloads(torch, pdilqr, dev, stream, args):
     lq["S"] = None
     sd = torch.tensor(np.asarray(s, np.float32), device=dev)
     wb = {"instances": len(allinst), "distinct": uniq, "n": 36, "m": 24, "N": 100}
-    for name, warps, fn_name in (("scan", 0, "kkt_scan_solve"), ("riccati", 1, "riccati_solve")):
-        plan = pdilqr.Plan(36, 24, Nv, off, warps=warps, refine=True)
+    refs = {}
+    for i in range(0, uniq, uniq // 8):         # eight distinct instances
+        r32 = {k: np.asarray(allinst[i][k], np.float32).astype(np.float64) for k in synth.LQ_KEYS}
+        refs[i] = oracle.riccati_solve(r32, np.asarray(s[i], np.float32).astype(np.float64))
+
+    def run(name, warps, fn_name, refine):
+        plan = pdilqr.Plan(36, 24, Nv, off, warps=warps, refine=refine)
         o = plan.alloc_out(device=dev, want_resid=True)
         fn = getattr(plan, fn_name)
         fn(lq, sd, out=o)
         torch.cuda.synchronize()
         t = event_times(torch, lambda: fn(lq, sd, out=o), 3, stream)
         bwd = pdilqr.backward_error(o["resid"]).cpu().numpy()
-        errs = []
-        dx = o["dx"].double().cpu().numpy()
-        for i in range(0, uniq, uniq // 8):     # eight distinct instances
+        z = {k: o[k].double().cpu().numpy() for k in ("dx", "du", "dlam")}
+        err = 0.0
+        for i, ref in refs.items():
             N, o0 = int(Nv[i]), int(off[i])
-            r32 = {k: np.asarray(allinst[i][k], np.float32).astype(np.float64) for k in synth.LQ_KEYS}
-            ref = oracle.riccati_solve(r32, np.asarray(s[i], np.float32).astype(np.float64))
-            errs.append(float(np.abs(dx[o0:o0 + N + 1] - ref["dx"]).max() / np.abs(ref["dx"]).max()))
-        wb[name] = {"kkt_solves_per_s": len(allinst) / (np.mean(t) / 1e3), "ms": float(np.mean(t)),
-                    "warps": plan.warps, "max_backward_error": float(bwd.max()),
-                    "max_rel_error_vs_oracle_sample": max(errs),
-                    "oracle_sample": "8 distinct instances (0, 16, ..., 112 of the 128)"}
+            for k, rk, n_slots in (("dx", "dx", N + 1), ("du", "du", N), ("dlam", "dlam", N + 1)):
+                got, want = z[k][o0:o0 + n_slots], ref[rk][:n_slots]
+                err = max(err, float(np.abs(got - want).max() / np.abs(want).max()))
+        rec = {"kkt_solves_per_s": len(allinst) / (np.mean(t) / 1e3), "ms": float(np.mean(t)),
+               "warps": plan.warps, "max_backward_error": float(bwd.max()),
+               "max_rel_error_vs_oracle_sample": err}
         plan.close()
+        return rec
+
+    for name, warps, fn_name in (("scan", 0, "kkt_scan_solve"), ("riccati", 1, "riccati_solve")):
+        wb[name] = run(name, warps, fn_name, True)
+        wb[name]["unrefined"] = run(name, warps, fn_name, False)
+        wb[name]["oracle_sample"] = ("8 distinct instances (0, 16, ..., 112 of the 128); error = "
+                                     "max over dx, du, dlam of |z - z_ref|_inf / |z_ref|_inf")
+    wb["note"] = ("refined: one correction solve against the FP64 KKT residual; unrefined: the "
+                  "FP32 solve alone (both timings include the final FP64 residual for the "
+                  "backward error)")
     out["whole_body_lq_batch"] = wb
     # single LQR (n = 4, m = 2, N = 16), graph replays
     inst = synth.ltv_lq(4, 2, 16, seed=0, **{k: v for k, v in synth.LQ_SMALL.items()
@@ -1007,6 +1021,8 @@ def main():
                          "--serve-seconds is 0)")
     ap.add_argument("--no-lq-workloads", dest="lq_workloads", action="store_false",
                     help="skip the whole-body LQ batch and single-LQR measurements")
+    ap.add_argument("--lq-only", action="store_true",
+                    help="print the LQ-solve workloads (whole-body-sized batch, single LQR) only")
     ap.add_argument("--sweep-reps", type=int, default=20,
                     help="graph replays per point of the horizon / robot-count sweep that the "
                          "bench line carries (0: leave it out)")
@@ -1022,6 +1038,13 @@ def main():
         return
     if args.peaks:
         print(json.dumps(run_peaks(args)), flush=True)
+        return
+    if args.lq_only:
+        import torch
+        from paper_2506_07823_b300 import pdilqr
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_lq_workloads(torch, pdilqr, torch.device("cuda", 0),
+                                              torch.cuda.current_stream(), args)), flush=True)
         return
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:
