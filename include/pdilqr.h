@@ -110,8 +110,13 @@ PDILQR_API int32_t pdilqr_plan_warps(const pdilqr_plan *plan);
  *   n >= 96) issue neither their MMAs nor the commit that signals them, so the
  *   bounded wait for them runs out (after about 0.6 s per CTA); the instance
  *   then ends with status PDILQR_E_TIMEOUT and the context stays usable.
+ *   PDILQR_DEBUG_BULK_SKIP_ISSUE: the one-CTA Riccati recursion of n = 24 and 36
+ *   (pdilqr_riccati_solve) issues none of its bulk stage copies, so the
+ *   bounded wait for the first one runs out (about 0.6 s per CTA); the
+ *   instance ends with status PDILQR_E_TIMEOUT and the context stays usable.
  * Errors: INVALID_ARG (unknown bits). */
 #define PDILQR_DEBUG_TC_SKIP_ISSUE 1
+#define PDILQR_DEBUG_BULK_SKIP_ISSUE 2
 PDILQR_API pdilqr_status pdilqr_plan_set_debug(pdilqr_plan *plan, int32_t flags);
 
 /* ------------------------------------------------------- LQ KKT solves */

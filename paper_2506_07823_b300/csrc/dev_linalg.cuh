@@ -176,6 +176,40 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// ------------------------------------------------ bulk copies (TMA engine)
+// One-dimensional bulk copy from global to this CTA's shared memory on the
+// tensor memory accelerator, completing as transaction bytes on an mbarrier.
+// dst and src must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
+
+// mbarrier with `count` arrivals per phase (call from one thread, then make
+// the initialisation visible with mbar_init_fence and a CTA barrier).
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// The calling thread's arrival on the current phase, announcing `bytes` of
+// bulk copies that complete on it.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// Orders this thread's earlier shared-memory accesses (generic proxy) before
+// later bulk copies into the same locations (async proxy).
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Allocate ncols columns (TMEM_TILE per 128-row tile of the largest
 // product; a power of two, at most 512) and set up the barrier (all threads
 // of the CTA).

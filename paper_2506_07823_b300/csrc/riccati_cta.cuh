@@ -126,23 +126,30 @@ __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d
 
 
 // ------------------------------------------------------------ one stage
-// Stage gs's A, B, c, q, r (and S) into the input bank `in` (asynchronous
-// copies, committed as one group; the caller waits).
+// Stage gs's A, B, c, q, r (and S) into the input bank `in`: one thread
+// issues one bulk copy per array on the TMA engine, all completing on the
+// bank's mbarrier (every array is contiguous per stage; sizes and offsets are
+// multiples of 16 bytes and the base pointers are 16-byte aligned, checked
+// at the boundary).
 template <int NX, int NU>
-__device__ __forceinline__ void rc_load(float* in, const KktArgs& a, int64_t gs, bool has_S, int t)
+struct RcBulk {
+    static constexpr uint32_t A = NX * NX * 4, B = NX * NU * 4, S = NU * NX * 4, c = NX * 4,
+                              q = NX * 4, r = NU * 4;
+    static_assert(A % 16 == 0 && B % 16 == 0 && c % 16 == 0 && r % 16 == 0, "bulk copy sizes");
+};
+
+template <int NX, int NU>
+__device__ __forceinline__ void rc_load(float* in, uint64_t* mbar, const KktArgs& a, int64_t gs, bool has_S)
 {
     using L = RicCtaL<NX, NU>;
-    for (int e = t; e < NX * NX / 4; e += kRcThreads)
-        cp_async16(in + L::A + 4 * e, a.A + gs * NX * NX + 4 * e);
-    for (int e = t; e < NX * NU / 4; e += kRcThreads)
-        cp_async16(in + L::Bm + 4 * e, a.B + gs * NX * NU + 4 * e);
-    if (has_S)
-        for (int e = t; e < NU * NX / 4; e += kRcThreads)
-            cp_async16(in + L::S + 4 * e, a.S + gs * NU * NX + 4 * e);
-    if (t < NX / 4) cp_async16(in + L::c + 4 * t, a.c + gs * NX + 4 * t);
-    else if (t < NX / 2) cp_async16(in + L::q + 4 * (t - NX / 4), a.q + gs * NX + 4 * (t - NX / 4));
-    else if (t < NX / 2 + NU / 4) cp_async16(in + L::r + 4 * (t - NX / 2), a.r + gs * NU + 4 * (t - NX / 2));
-    cp_async_commit();
+    using Z = RcBulk<NX, NU>;
+    mbar_arrive_expect_tx(mbar, Z::A + Z::B + Z::c + Z::q + Z::r + (has_S ? Z::S : 0u));
+    bulk_g2s(in + L::A, a.A + gs * NX * NX, Z::A, mbar);
+    bulk_g2s(in + L::Bm, a.B + gs * NX * NU, Z::B, mbar);
+    if (has_S) bulk_g2s(in + L::S, a.S + gs * NU * NX, Z::S, mbar);
+    bulk_g2s(in + L::c, a.c + gs * NX, Z::c, mbar);
+    bulk_g2s(in + L::q, a.q + gs * NX, Z::q, mbar);
+    bulk_g2s(in + L::r, a.r + gs * NU, Z::r, mbar);
 }
 
 // Product 1: Y = P'[A | B] (6 x 4 tiles), w = P'c + p', t = A^T p', and the
@@ -410,7 +417,9 @@ __device__ __forceinline__ void rc_product5(float* sm, const float* in, const Kk
 // ------------------------------------------------------------ kernel
 // One CTA of 128 threads per instance (slot blockIdx.x of the longest-first
 // order): the terminal value function, N backward steps (stage k - 1's
-// inputs are copied into the other bank while stage k is processed), then
+// inputs are bulk-copied into the other bank while stage k is processed;
+// a copy that does not land within the bounded wait ends the instance with
+// status TIMEOUT), then
 // the forward rollout dx_{k+1} = Abar_k dx_k + bbar_k with du_k = K_k dx_k +
 // k_k and dlam_k = P_k dx_k + p_k.  Status: NOT_SPD if a pivot of some G_k
 // was not positive, NONFINITE if an output is not finite.
@@ -419,6 +428,7 @@ __global__ void __launch_bounds__(kRcThreads, 4) riccati_cta_kernel(const __grid
 {
     using L = RicCtaL<NX, NU>;
     extern __shared__ __align__(16) float sm[];
+    __shared__ uint64_t mbar[2];   // one per input bank
     const int t = threadIdx.x;
     const int slot = blockIdx.x;
     if (slot >= a.count) return;
@@ -426,7 +436,16 @@ __global__ void __launch_bounds__(kRcThreads, 4) riccati_cta_kernel(const __grid
     const int N = a.N[inst];
     const int64_t off = a.off[inst];
     const bool has_S = a.S != nullptr;
-    if (N > 0) rc_load<NX, NU>(sm + ((N - 1) & 1) * L::IN, a, off + N - 1, has_S, t);
+    // test switch: no bulk copy is issued, so the first bounded wait runs out
+    const bool issue = (a.dbg & PDILQR_DEBUG_BULK_SKIP_ISSUE) == 0;
+    if (t == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (t == 0 && N > 0 && issue)
+        rc_load<NX, NU>(sm + ((N - 1) & 1) * L::IN, &mbar[(N - 1) & 1], a, off + N - 1, has_S);
     {
         const int64_t gN = off + N;
         for (int e = t; e < NX * NX / 4; e += kRcThreads) {
@@ -442,14 +461,27 @@ __global__ void __launch_bounds__(kRcThreads, 4) riccati_cta_kernel(const __grid
         for (int e = t; e < NU * NX; e += kRcThreads) a.K[gN * NU * NX + e] = 0.f;
         for (int i = t; i < NU; i += kRcThreads) a.k[gN * NU + i] = 0.f;
     }
-    bool spd = true;
+    bool spd = true, timed_out = false;
+    uint32_t phase = 0;   // bit b: the parity bank b's next wait expects
     for (int k = N - 1; k >= 0; --k) {
         const int64_t gs = off + k;
-        float* in = sm + (k & 1) * L::IN;
-        // stage k's copies have landed; the other bank (stage k + 1's) is free
-        cp_async_wait_all();
-        __syncthreads();
-        if (k > 0) rc_load<NX, NU>(sm + ((k - 1) & 1) * L::IN, a, gs - 1, has_S, t);
+        const int b = k & 1;
+        float* in = sm + b * L::IN;
+        // stage k's copies have landed (bounded wait, one verdict for the CTA)
+        const bool got = mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, kTcWaitNs);
+        // the other bank (stage k + 1's) is free once every thread is here;
+        // its generic-proxy writes (Abar, bbar in place) are ordered before
+        // the bulk copies that overwrite it
+        fence_proxy_async_smem();
+        if (__syncthreads_or(got ? 0 : 1)) {
+            // the copies of bank b (the only ones in flight) get a second
+            // bounded wait before the CTA gives up its shared memory
+            mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, kTcDrainNs);
+            timed_out = true;
+            break;
+        }
+        phase ^= 1u << b;
+        if (t == 0 && k > 0 && issue) rc_load<NX, NU>(sm + (b ^ 1) * L::IN, &mbar[b ^ 1], a, gs - 1, has_S);
         rc_product1<NX, NU>(sm, in, t);
         __syncthreads();
         for (int task = t; task < RcP2<NX, NU>::TASKS; task += kRcThreads)
@@ -463,7 +495,10 @@ __global__ void __launch_bounds__(kRcThreads, 4) riccati_cta_kernel(const __grid
         for (int task = t; task < RcP5<NX, NU>::TASKS; task += kRcThreads)
             rc_product5<NX, NU>(sm, in, a, gs, has_S, task);
     }
-    cp_async_wait_all();
+    if (timed_out) {
+        if (t == 0) a.status[inst] = ST_TIMEOUT;
+        return;
+    }
     __syncthreads();
     // forward rollout from dx_0 = s over the stored stages (the global stores
     // of this CTA are visible to its own later loads after the barrier)

@@ -268,3 +268,39 @@ def test_nonfinite_status(solver, n, m):
     sub = {k: out[k] for k in ("dx", "du", "dlam")}
     sub["status"] = out["status"][keep]
     check_parity([insts[i] for i in keep], Nv[keep], off[keep], sub, s[keep], False)
+
+
+@pytest.mark.parametrize("n,m", [(24, 24), (36, 24)])
+def test_bulk_copy_timeout_status(n, m):
+    """The one-CTA recursion's stage copies go through the TMA engine with a
+    bounded wait: with the test switch that issues none of them, every
+    instance ends with E_TIMEOUT (nothing is in flight), and the same plan
+    then solves normally."""
+    from paper_2506_07823_b300 import pdilqr
+    insts, packed, Nv, off, s = make_batch(n, m, [5, 3], seed=71)
+    plan = pdilqr.Plan(n, m, Nv, off)
+    lq, sd = to_dev(packed, s, False)
+    plan.set_debug(pdilqr.DEBUG_BULK_SKIP_ISSUE)
+    out = plan.riccati_solve(lq, sd)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == pdilqr.E_TIMEOUT)
+    plan.set_debug(0)
+    out = plan.riccati_solve(lq, sd)
+    torch.cuda.synchronize()
+    check_parity(insts, Nv, off, out, s, False)
+
+
+def test_misaligned_arrays_are_rejected():
+    """Every per-stage array is read with 16-byte accesses: a pointer that is
+    not 16-byte aligned is an invalid argument (no launch)."""
+    from paper_2506_07823_b300 import pdilqr
+    n, m = 36, 24
+    insts, packed, Nv, off, s = make_batch(n, m, [4], seed=72)
+    plan = pdilqr.Plan(n, m, Nv, off)
+    lq, sd = to_dev(packed, s, False)
+    base = lq["q"]
+    shifted = torch.empty(base.numel() + 1, device="cuda", dtype=torch.float32)
+    shifted[1:].copy_(base.reshape(-1))
+    lq["q"] = shifted[1:].reshape(base.shape)
+    with pytest.raises(pdilqr.PdilqrError, match="INVALID_ARG"):
+        plan.riccati_solve(lq, sd)
