@@ -66,9 +66,15 @@ struct RowRicL {
 // Abar, bbar are written to global memory at stage slot gs (Abar, bbar also
 // to abar_sm when given: N rows, then N floats).  Returns false (uniformly
 // over the half) if G is not SPD.
+//
+// lam1 (optional, n floats): the costate lam_{k+1} when the stage's q and r
+// leave out their terms A^T lam_{k+1} and B^T lam_{k+1} (srbd_lin_rows12).
+// Both enter the step only through A^T w and B^T w with w = p' + P'c, so
+// adding lam_{k+1} to w adds them exactly where they belong.
 template <int N>
 __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, const KktArgs& a,
-                             int64_t gs, bool has_S, float* abar_sm = nullptr)
+                             int64_t gs, bool has_S, float* abar_sm = nullptr,
+                             const float* lam1 = nullptr)
 {
     using L = StageL<N, N>;
     using S = RowRicL<N>;
@@ -83,21 +89,29 @@ __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, cons
         float pa[N], pb[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) { pa[j] = 0.f; pb[j] = 0.f; }
-        float Pr[N];
-        ld_row(Pr, scr + S::V + r * N);
         float wr = scr[S::vp + r];
+        if (lam1) wr += lam1[r];
+        // blocks of four rows l (the loop over blocks is not unrolled: a
+        // smaller body keeps the two warps of a scheduler in the
+        // instruction cache)
+#pragma unroll 1
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 p4 = reinterpret_cast<const float4*>(scr + S::V + r * N)[q];
+            const float4 c4 = reinterpret_cast<const float4*>(st + L::c)[q];
+            const float pq[4] = {p4.x, p4.y, p4.z, p4.w}, cq[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-        for (int l = 0; l < N; ++l) {
-            float al[N], bl[N];
-            ld_row(al, st + L::A + l * N);
-            ld_row(bl, st + L::B + l * N);
-            const float prl = Pr[l];
+            for (int i = 0; i < 4; ++i) {
+                const int l = 4 * q + i;
+                float al[N], bl[N];
+                ld_row(al, st + L::A + l * N);
+                ld_row(bl, st + L::B + l * N);
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                pa[j] = fmaf(prl, al[j], pa[j]);
-                pb[j] = fmaf(prl, bl[j], pb[j]);
+                for (int j = 0; j < N; ++j) {
+                    pa[j] = fmaf(pq[i], al[j], pa[j]);
+                    pb[j] = fmaf(pq[i], bl[j], pb[j]);
+                }
+                wr = fmaf(pq[i], cq[i], wr);
             }
-            wr = fmaf(prl, st[L::c + l], wr);
         }
         st_row(PA + r * N, pa);
         st_row(PB + r * N, pb);
@@ -117,7 +131,7 @@ __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, cons
         ps = st[L::q + r];
         // two passes over the rows (G, h from P'B; H, P, p from P'A) keep
         // fewer accumulators live
-#pragma unroll
+#pragma unroll 4
         for (int l = 0; l < N; ++l) {
             const float blr = st[L::B + l * N + r];
             float pbl[N];
@@ -126,7 +140,7 @@ __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, cons
             for (int j = 0; j < N; ++j) gr[j] = fmaf(blr, pbl[j], gr[j]);
             hs = fmaf(blr, w[l], hs);
         }
-#pragma unroll
+#pragma unroll 4
         for (int l = 0; l < N; ++l) {
             const float blr = st[L::B + l * N + r], alr = st[L::A + l * N + r];
             float pal[N];
@@ -148,18 +162,23 @@ __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, cons
     }
     // (c) G^-1 [H | h] by Gauss-Jordan elimination without pivoting, row r
     // per lane; at step k every other row subtracts its multiple of row k,
-    // whose entries right of the pivot come from lane k by shuffles (no
-    // shared-memory round trip or barrier); the pivot row is not normalised
+    // whose entries come from lane k by shuffles (no shared-memory round
+    // trip or barrier); the pivot row is not normalised.  Column k of G is
+    // not needed after step k, so every step shifts the row's remaining
+    // columns of G left by one: the pivot column is always gr[0], and the
+    // loop over k needs no unrolling (a small body for the instruction
+    // cache, at the price of updating the dead columns too).
     bool ok = true;
     float dr = 1.f;
-#pragma unroll
+#pragma unroll 3
     for (int k = 0; k < N; ++k) {
-        const float pk = __shfl_sync(g.mask, gr[k], k, 16);
+        const float pk = __shfl_sync(g.mask, gr[0], k, 16);
         ok = ok && (pk > 0.f) && isfinite(pk);
         if (r == k) dr = pk;
-        const float f = (row && r != k) ? gr[k] * rcp_approx(pk) : 0.f;
+        const float f = (row && r != k) ? gr[0] * rcp_approx(pk) : 0.f;
 #pragma unroll
-        for (int j = k + 1; j < N; ++j) gr[j] = fmaf(-f, __shfl_sync(g.mask, gr[j], k, 16), gr[j]);
+        for (int j = 1; j < N; ++j) gr[j - 1] = fmaf(-f, __shfl_sync(g.mask, gr[j], k, 16), gr[j]);
+        gr[N - 1] = 0.f;
 #pragma unroll
         for (int j = 0; j < N; ++j) hr[j] = fmaf(-f, __shfl_sync(g.mask, hr[j], k, 16), hr[j]);
         hs = fmaf(-f, __shfl_sync(g.mask, hs, k, 16), hs);
@@ -183,23 +202,28 @@ __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, cons
     // Abar = A - B Y, bbar = c - B y (row r of B against the rows of Y)
     float* Pt = scr + S::Pt;
     if (row) {
-        float br[N], ab[N];
-        ld_row(br, st + L::B + r * N);
+        float ab[N];
         ld_row(ab, st + L::A + r * N);
         float bb = st[L::c + r];
+#pragma unroll 1
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 b4 = reinterpret_cast<const float4*>(st + L::B + r * N)[q];
+            const float4 y4 = reinterpret_cast<const float4*>(yv)[q];
+            const float bq[4] = {b4.x, b4.y, b4.z, b4.w}, yq[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-        for (int l = 0; l < N; ++l) {
-            const float hlr = H[l * N + r];
-            float yl[N];
-            ld_row(yl, Y + l * N);
-            const float yvl = yv[l];
+            for (int i = 0; i < 4; ++i) {
+                const int l = 4 * q + i;
+                const float hlr = H[l * N + r];
+                float yl[N];
+                ld_row(yl, Y + l * N);
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                pn[j] = fmaf(-hlr, yl[j], pn[j]);
-                ab[j] = fmaf(-br[l], yl[j], ab[j]);
+                for (int j = 0; j < N; ++j) {
+                    pn[j] = fmaf(-hlr, yl[j], pn[j]);
+                    ab[j] = fmaf(-bq[i], yl[j], ab[j]);
+                }
+                ps = fmaf(-hlr, yq[i], ps);
+                bb = fmaf(-bq[i], yq[i], bb);
             }
-            ps = fmaf(-hlr, yvl, ps);
-            bb = fmaf(-br[l], yvl, bb);
         }
         st_row(Pt + r * N, pn);
         st_row(a.Abar + gs * N * N + r * N, ab);
@@ -221,6 +245,156 @@ __device__ bool riccati_rows(const Grp<16>& g, const float* st, float* scr, cons
         a.p[gs * N + r] = ps;
     }
     return ok;
+}
+
+// ----------------------------------------- linearisation, one robot, rows
+// Entry c of {v0, v1, v2} for a lane-dependent c, by selects (a dynamic
+// index into a register array would go through local memory).
+__device__ __forceinline__ float pick3(float v0, float v1, float v2, int c)
+{
+    return c == 0 ? v0 : (c == 1 ? v1 : v2);
+}
+
+// Row a of the cross-product matrix [v]x (rows (0, -v2, v1), (v2, 0, -v0),
+// (-v1, v0, 0)), a lane-dependent.
+__device__ __forceinline__ void skew_row(const float (&v)[3], int a, float (&o)[3])
+{
+    o[0] = a == 1 ? v[2] : (a == 2 ? -v[1] : 0.f);
+    o[1] = a == 0 ? -v[2] : (a == 2 ? v[0] : 0.f);
+    o[2] = a == 0 ? v[1] : (a == 1 ? -v[0] : 0.f);
+}
+
+// One stage of the single-robot SRBD linearisation (Sec. II-B, II-F) by the
+// 16 lanes of a half-warp: lane r < 12 writes row r of A, B, Q and R and
+// c_r, q_r, r_r into st (StageL<12, 12>) from the closed-form derivatives of
+// srbd_linearize_stage, selecting its row's terms instead of branching on r,
+// so that the lanes stay converged:
+//   A = I + dt df/dx:  rows 0..5: e_r + dt e_{r+6} (p' = v, theta' = w);
+//     rows 9..11 (a = r - 9): e_r + dt I_a^-1 ([F]x row a at p, -([w]x I -
+//     [I w]x) row a at w), F = sum of the stance forces;
+//   B = dt df/du:  rows 6..8: dt / mass at the stance feet's component r - 6;
+//     rows 9..11: dt I_a^-1 [foot_j - p]x row a at stance foot j;
+//   c_r = (x_r - x_{k+1, r}) + dt f_r(x, u);
+//   Q = diag(W) (W_N at the terminal), q_r = W_r (x_r - xref_r) - lam_{k,r};
+//   R = diag(W_u) + the barrier curvature of the friction pyramid (3 x 3
+//   block of the lane's foot), r_r = W_u,r (u_r - uref_r) + barrier slope.
+// The costate terms A^T lam_{k+1} of q and B^T lam_{k+1} of r are left out:
+// riccati_rows adds lam_{k+1} to p' + P'c, which both terms multiply.  The
+// model inputs come from an input buffer filled by SrbdSource::fetch (x, x1,
+// lam_k, lam_{k+1}, xref, u, uref, contact); nothing is read at the terminal
+// beyond x, lam_k and xref.
+__device__ __forceinline__ void srbd_lin_rows12(const Grp<16>& g, float* st,
+                                                const pdilqr_srbd_model& md, const float* in,
+                                                bool terminal)
+{
+    using L = StageL<12, 12>;
+    const int r = g.t;
+    if (r >= 12) return;
+    const float* x = in;
+    const float* x1 = in + 12;
+    const float* l0 = in + 24;
+    const float* xr = in + 48;
+    const float* u = in + 60;
+    const float* ur = in + 72;
+    const uint8_t* ct = reinterpret_cast<const uint8_t*>(in + 84);
+    float row[12];
+    // Q row r and q_r
+    const float wq = terminal ? md.WN[r] : md.W[r];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) row[j] = j == r ? wq : 0.f;
+    st_row(st + L::Q + r * 12, row);
+    st[L::q + r] = wq * (x[r] - xr[r]) - l0[r];
+    if (terminal) return;
+
+    const float dt = md.dt;
+    float p[3], w[3], sv[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { p[i] = x[i]; w[i] = x[9 + i]; }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sv[j] = ct[j] ? 1.f : 0.f;
+    // stance force sum F and torque sum tau = sum_j s_j (foot_j - p) x f_j
+    float F[3] = {0.f, 0.f, 0.f}, tau[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float f[3] = {u[3 * j] * sv[j], u[3 * j + 1] * sv[j], u[3 * j + 2] * sv[j]};
+        const float arm[3] = {md.foot[j][0] - p[0], md.foot[j][1] - p[1], md.foot[j][2] - p[2]};
+        float t[3];
+        cross3f(arm, f, t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { F[i] += f[i]; tau[i] += t[i]; }
+    }
+    const float Iw[3] = {md.inertia[0] * w[0], md.inertia[1] * w[1], md.inertia[2] * w[2]};
+    float gyro[3];
+    cross3f(w, Iw, gyro);
+    const bool ang = r >= 9, lin = r >= 6 && r < 9;
+    const int a = ang ? r - 9 : 0;      // angular row's axis
+    const int b = lin ? r - 6 : 0;      // linear-velocity row's axis
+    const float Ia = pick3(md.inertia[0], md.inertia[1], md.inertia[2], a);
+    const float sc = dt * rcp_approx(Ia);
+    const float dtm = dt * rcp_approx(md.mass);
+    // c_r = (x_r - x1_r) + dt f_r
+    float fr;
+    if (r < 6) fr = x[r + 6];
+    else if (lin) fr = pick3(F[0], F[1], F[2], b) / md.mass - (b == 2 ? md.gravity : 0.f);
+    else fr = (pick3(tau[0], tau[1], tau[2], a) - pick3(gyro[0], gyro[1], gyro[2], a)) / Ia;
+    st[L::c + r] = (x[r] - x1[r]) + dt * fr;
+    // A row r
+    {
+        float sF[3], sw[3], sIw[3];
+        skew_row(F, a, sF);
+        skew_row(w, a, sw);
+        skew_row(Iw, a, sIw);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) row[j] = (j == r ? 1.f : 0.f) + (r < 6 && j == r + 6 ? dt : 0.f);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            row[l] += ang ? sc * sF[l] : 0.f;
+            row[9 + l] -= ang ? sc * (sw[l] * md.inertia[l] - sIw[l]) : 0.f;
+        }
+        st_row(st + L::A + r * 12, row);
+    }
+    // B row r
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float arm[3] = {md.foot[j][0] - p[0], md.foot[j][1] - p[1], md.foot[j][2] - p[2]};
+        float sa[3];
+        skew_row(arm, a, sa);
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            row[3 * j + l] = sv[j] * (ang ? sc * sa[l] : (lin && l == b ? dtm : 0.f));
+    }
+    st_row(st + L::B + r * 12, row);
+    // R row r and r_r: control r is component cp of foot jf
+    const int jf = r / 3, cp = r - 3 * jf;
+    const float wu = md.Wu[r];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) row[j] = j == r ? wu : 0.f;
+    float grad = wu * (u[r] - ur[r]);
+    if (ct[jf]) {
+        const float f0 = u[3 * jf], f1 = u[3 * jf + 1], f2 = u[3 * jf + 2];
+        const float mu = md.mu_fric;
+        float blk[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float g0 = cone_g(c, 0, mu), g1 = cone_g(c, 1, mu), g2 = cone_g(c, 2, mu);
+            const float xi = g0 * f0 + g1 * f1 + g2 * f2;
+            const bool hi = xi >= md.bar_delta;
+            const float iv = rcp_approx(hi ? xi : md.bar_delta);
+            const float d1 = hi ? -md.bar_mu * iv : md.bar_mu * (xi - 2.f * md.bar_delta) * iv * iv;
+            const float d2 = md.bar_mu * iv * iv;
+            const float gc = pick3(g0, g1, g2, cp);
+            grad += d1 * gc;
+            blk[0] += d2 * gc * g0;
+            blk[1] += d2 * gc * g1;
+            blk[2] += d2 * gc * g2;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) row[3 * j + l] += j == jf ? blk[l] : 0.f;
+    }
+    st_row(st + L::R + r * 12, row);
+    st[L::r + r] = grad;
 }
 
 // ------------------------------------------------------ merit, one half
@@ -566,6 +740,24 @@ __device__ bool rollout_rows(const Grp<16>& g, const KktArgs& ka, int64_t off, i
     return fin;
 }
 
+// Linearise the stage whose inputs are in `in` into st: the one-robot row
+// form (costate terms left to the Riccati step) at n = 12, else the generic
+// row-parallel linearisation.  PENDING: copy groups committed after this
+// stage's.
+template <int NX, int PENDING>
+__device__ __forceinline__ void lin_stage(const Grp<16>& g, const SrbdSource& src, float* st,
+                                          const float* in, bool terminal)
+{
+    if constexpr (NX == 12) {
+        cp_async_wait<PENDING>();
+        g.sync();
+        srbd_lin_rows12(g, st, src.md, in, terminal);
+        g.sync();
+    } else {
+        src.template linearize<NX, NX, 16, PENDING>(g, st, in, terminal);
+    }
+}
+
 // ------------------------------------------------------------- the kernel
 template <int NX>
 struct SqpRowsSmem {
@@ -631,7 +823,7 @@ __device__ __forceinline__ void sqp_rows_instance(const SqpArgs& a, const Grp<16
         float* inb = base + SM::INB;
         src.template fetch<NX, NU, 16>(g, inb + (N & 1) * SM::INF, off + N, true);
         if (N >= 1) src.template fetch<NX, NU, 16>(g, inb + ((N - 1) & 1) * SM::INF, off + N - 1, false);
-        src.template linearize<NX, NU, 16, 1>(g, st, inb + (N & 1) * SM::INF, true);
+        lin_stage<NX, 1>(g, src, st, inb + (N & 1) * SM::INF, true);
         if (row) {
             float PN[NX];
             ld_row(PN, st + L::Q + r * NX);
@@ -644,13 +836,17 @@ __device__ __forceinline__ void sqp_rows_instance(const SqpArgs& a, const Grp<16
         bool ok = true;
         for (int k = N - 1; k >= 0; --k) {
             g.sync();   // every read of the previous stage is done
+            const float* ink = inb + (k & 1) * SM::INF;
             if (k >= 1) {
                 src.template fetch<NX, NU, 16>(g, inb + ((k - 1) & 1) * SM::INF, off + k - 1, false);
-                src.template linearize<NX, NU, 16, 1>(g, st, inb + (k & 1) * SM::INF, false);
+                lin_stage<NX, 1>(g, src, st, ink, false);
             } else {
-                src.template linearize<NX, NU, 16, 0>(g, st, inb + (k & 1) * SM::INF, false);
+                lin_stage<NX, 0>(g, src, st, ink, false);
             }
-            ok = riccati_rows<NX>(g, st, scr, ka, off + k, false) && ok;
+            // lam_{k+1} of the input buffer when the linearisation left out
+            // the costate terms (the one-robot row form)
+            const float* l1 = NX == 12 ? ink + 3 * 12 : nullptr;
+            ok = riccati_rows<NX>(g, st, scr, ka, off + k, false, nullptr, l1) && ok;
         }
         if (!ok) {
             status = ST_NOT_SPD;
