@@ -86,6 +86,18 @@ typedef struct {
                         /* kernels (the comparator of the fused solver)     */
     int32_t refine;     /* 0: plain FP32 solve; 1: one refinement step      */
                         /* against the FP64-evaluated KKT residual          */
+    int32_t inst_per_cta; /* instances per CTA of the batched sequential    */
+                        /* SQP of one-robot SRBD problems (n = m = 12,      */
+                        /* warps = 1): 2, 4 or 8 (CTAs of 1, 2 or 4 warps,  */
+                        /* two instances per warp); 0 picks 2.  Other       */
+                        /* solvers take one instance per CTA and require 0. */
+    int32_t m_fp64;     /* 1: the scan's combines (Sec. II-D, Eq.            */
+                        /* combination_rule) factor M = I + C1 P2 and apply  */
+                        /* M^-1 to [A1 | C1 | b1 - C1 p2] by Gauss-Jordan   */
+                        /* elimination with partial pivoting in FP64 (the    */
+                        /* FP32 entries widened once, results rounded back); */
+                        /* 0: in FP32.  Only (n, m) = (36, 24); other sizes  */
+                        /* require 0.  The Riccati solver is unaffected.     */
 } pdilqr_opts;
 
 typedef struct pdilqr_plan pdilqr_plan;
@@ -335,8 +347,9 @@ typedef struct {
     int32_t max_batch;         /* requests per launch (0: 1024; 1: one per launch);
                                   a class of 2^c robots takes at most
                                   max(64, max_batch / 4^c), never above max_batch */
-    int32_t max_inflight;      /* batches in flight on separate streams (0: 2);
-                                  classes of 4+ robots hold at most all but one */
+    int32_t max_inflight;      /* batches in flight on separate streams, 1..16
+                                  (0: 2); classes of 4+ robots hold at most all
+                                  but one */
     int32_t max_N;             /* longest horizon a client may use (0: 100)       */
     int32_t sqp_iters;         /* SQP iterations per request (0: 1)               */
     int32_t warps;             /* horizon chunks per instance, an upper bound    */

@@ -831,6 +831,81 @@ __device__ bool gj_solve_generic(const Grp<NT>& g, float* G, int ld, float* wsc)
     return ok;
 }
 
+// Gauss-Jordan elimination with partial pivoting of [M | RHS] (N rows, N + NR
+// columns, row-major with leading dimension ld) in FP64: the FP32 entries
+// are widened once and every thread of the group holds one column in FP64
+// registers for the whole elimination.  Rows are exchanged implicitly: the
+// pivot row of step k is recorded (prow[k]), not moved, so no register array
+// is indexed by a run-time row.  At step k the owner of column k publishes
+// that column (the multipliers) and its pivot row, chosen by the largest
+// magnitude among the rows not yet used, to a double-buffered FP64 area; the
+// owner of column k + 1 publishes the next one right after its own update,
+// so a step costs one barrier.  Every column j > k then divides its entry in
+// the pivot row by the pivot and subtracts the multiples from the other rows.
+// On exit the pivot row of step k holds row k of M^-1 RHS, which is written
+// back (rounded to FP32) over G's columns N.. at row k.  dbuf: 2 N doubles +
+// 2 N ints of shared memory (or work-area memory).  Returns false (uniformly)
+// if a pivot's magnitude is below 1e-300 or not finite.
+template <int N, int NR, int NT>
+__device__ bool gj_solve_f64(const Grp<NT>& g, float* G, int ld, double* dbuf)
+{
+    constexpr int W = N + NR;
+    static_assert(W <= NT, "one column per thread");
+    static_assert(N <= 64, "used rows as a 64-bit mask");
+    double* mcol = dbuf;                                  // [2][N] multiplier columns
+    int* prow = reinterpret_cast<int*>(dbuf + 2 * N);    // [N] pivot row of step k
+    int* rank = prow + N;                                 // [N] step at which row i pivots
+    const int j = g.t;
+    const bool mine = j < W;
+    double c[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) c[i] = mine ? (double)G[(size_t)i * ld + j] : 0.0;
+    uint64_t used = 0;
+    // the owner of column k: its column as multipliers, the pivot row
+    auto publish = [&](int k) {
+        double* m = mcol + (k & 1) * N;
+        double best = -1.0;
+        int bi = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            m[i] = c[i];
+            const double a = fabs(c[i]);
+            if (!((used >> i) & 1) && a > best) { best = a; bi = i; }
+        }
+        prow[k] = bi;
+    };
+    if (j == 0) publish(0);
+    g.sync();
+    bool ok = true;
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+        const double* m = mcol + (k & 1) * N;
+        const int p = prow[k];
+        const double piv = m[p];
+        ok = ok && fabs(piv) > 1e-300 && isfinite(piv);
+        if (mine && j > k) {
+            double vp = 0.0;
+#pragma unroll
+            for (int i = 0; i < N; ++i) vp = i == p ? c[i] : vp;
+            const double rk = vp / piv;
+#pragma unroll
+            for (int i = 0; i < N; ++i) c[i] = i == p ? rk : fma(-m[i], rk, c[i]);
+        }
+        used |= uint64_t(1) << p;
+        if (j == k + 1 && k + 1 < N) publish(k + 1);
+        g.sync();
+    }
+    if (j == 0)
+        for (int k = 0; k < N; ++k) rank[prow[k]] = k;
+    g.sync();
+    if (mine && j >= N) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) G[(size_t)rank[i] * ld + j] = (float)c[i];
+    }
+    g.sync();
+    return ok;
+}
+
 // ---------------------------------------------------------------------------
 // One-warp versions: operands live in registers, one row or one column per
 // lane, so the sequential steps need no index arithmetic and few barriers.

@@ -63,6 +63,8 @@ struct KktArgs {
     float* gws;                                  // per-CTA work areas in global memory
                                                  // (sizes whose areas exceed shared memory)
     int dbg;                                     // test switches (PDILQR_DEBUG_*), normally 0
+    int m64 = 0;                                 // 1: the combines eliminate M = I + C1 P2
+                                                 // in FP64 (n = 36; gj_solve_f64)
 };
 
 // ------------------------------------------------------------------ layouts
@@ -285,13 +287,36 @@ __device__ bool build_element(const Grp<NT>& g, const float* st, float* e, float
 }
 
 // ----------------------------------------------------------------- combines
+// M^-1 [RHS] of a combine (Eq. combination_rule): the FP32 elimination, or,
+// when m64 is set on a size that has it (n = 36, whose units of 128 threads
+// hold one column of [M | A1 | C1 | b] each), the FP64 one (gj_solve_f64),
+// its multiplier columns in the unit's shared tile buffer or else in the
+// combine scratch at dscr (T, unused until M^-1 has been applied).
+// (Out of line, so that its FP64 column registers do not weigh on the
+// register allocation of the FP32 path around it.)
+template <int NX, int NR, int NT>
+__device__ __noinline__ bool m_solve_f64(const Grp<NT>& g, float* G, int ld, double* dbuf)
+{
+    return gj_solve_f64<NX, NR, NT>(g, G, ld, dbuf);
+}
+
+template <int NX, int NR, int NT>
+__device__ __forceinline__ bool m_solve(const Grp<NT>& g, float* G, int ld, float* wsc,
+                                        float* dscr, bool m64)
+{
+    if constexpr (NX == 36 && NX + NR <= NT) {
+        if (m64) return m_solve_f64<NX, NR, NT>(g, G, ld, reinterpret_cast<double*>(g.tb ? g.tb : dscr));
+    }
+    return gj_solve<NX, NR, NT>(g, G, ld, wsc);
+}
+
 // out = e1 (x) e2 for two full elements (e1 earlier in time).  out must not
 // alias e2; it may alias e1 on the one-warp path through M^-1 (every read of
 // e1 there precedes the barrier before the first store to out, except the
 // addends P1, p1, which each thread reads at the places it then writes).
 template <int NX, int NT>
 __device__ bool combine_full(const Grp<NT>& g, const float* e1, const float* e2, float* out,
-                             float* scr)
+                             float* scr, bool m64 = false)
 {
     using E = ElemL<NX>;
     using S = CombL<NX>;
@@ -349,7 +374,7 @@ __device__ bool combine_full(const Grp<NT>& g, const float* e1, const float* e2,
     g.sync();
     for (int i = g.t; i < NX; i += NT) G[i * LDG + i] += 1.f;   // M = I + C1 P2
     g.sync();
-    const bool ok = gj_solve<NX, 2 * NX + 1, NT>(g, G, LDG, scr + S::Wk);
+    const bool ok = m_solve<NX, 2 * NX + 1, NT>(g, G, LDG, scr + S::Wk, scr + S::T, m64);
     const float* XA = G + NX;       // M^-1 A1
     const float* XC = G + 2 * NX;   // M^-1 C1
     const float* xb = G + 3 * NX;   // M^-1 (b1 - C1 p2)
@@ -370,7 +395,7 @@ __device__ bool combine_full(const Grp<NT>& g, const float* e1, const float* e2,
 // P = (M^-1 A1)^T P2 A1 + P1,  p = (M^-1 A1)^T (p2 + P2 b1) + p1.
 template <int NX, int NT>
 __device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, float* out,
-                           float* scr)
+                           float* scr, bool m64 = false)
 {
     using E = ElemL<NX>;
     using S = CombL<NX>;
@@ -385,7 +410,7 @@ __device__ bool combine_vf(const Grp<NT>& g, const float* e1, const float* v2, f
     g.sync();
     for (int i = g.t; i < NX; i += NT) G[i * LDG + i] += 1.f;
     g.sync();
-    const bool ok = gj_solve<NX, NX, NT>(g, G, LDG, scr + S::Wk);
+    const bool ok = m_solve<NX, NX, NT>(g, G, LDG, scr + S::Wk, scr + S::T, m64);
     const float* XA = G + NX;
     mm<NX, NX, NX, true, false, NT, false>(g, out + E::P, NX, XA, LDG, U, NX, e1 + E::P, NX);
     mm<NX, 1, NX, true, false, NT, false>(g, out + E::p, 1, XA, LDG, w, 1, e1 + E::p, 1);
@@ -728,7 +753,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
                 if (!build_element<NX, NU, NT, FAC>(g, stg, acc, bscr, has_S, false)) bad = ST_NOT_SPD;
             } else {
                 if (!build_element<NX, NU, NT, FAC>(g, stg, elem, bscr, has_S, false)) bad = ST_NOT_SPD;
-                if (!combine_full<NX, NT>(g, acc, elem, other, cscr)) bad = ST_SINGULAR;
+                if (!combine_full<NX, NT>(g, acc, elem, other, cscr, a.m64)) bad = ST_SINGULAR;
                 float* t = acc; acc = other; other = t;
             }
         }
@@ -784,8 +809,8 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
                 if (j + d < J) {
                     const bool vf = (j + 2 * d - 1 >= J - 1);
                     const float* e2 = src + (j + 1 + d) * ss;
-                    const bool ok = vf ? combine_vf<NX, NT>(g, e1, e2, out, scr)
-                                       : combine_full<NX, NT>(g, e1, e2, out, scr + SM::ELEM);
+                    const bool ok = vf ? combine_vf<NX, NT>(g, e1, e2, out, scr, a.m64)
+                                       : combine_full<NX, NT>(g, e1, e2, out, scr + SM::ELEM, a.m64);
                     if (!ok) bad = ST_SINGULAR;
                 } else {
                     copy<NX * NX + NX, 1, false, NT>(g, out + E::P, 1, e1 + E::P, 1);

@@ -265,16 +265,30 @@ static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
 }
 
 // The one-chunk (sequential recursion) fused SQP of small SRBD states: the
-// row-per-lane kernel, two instances per one-warp CTA.
+// row-per-lane kernel, two instances per warp, WPC warps per CTA.
+template <int NX, int WPC>
+static cudaError_t launch_sqp_rows_w(const SqpArgs& a, cudaStream_t st)
+{
+    constexpr size_t bytes = WPC * SqpRowsSmem<NX>::BYTES;
+    static std::atomic<uint64_t> smem_done{0};
+    if (cudaError_t e = ensure_smem(sqp_rows_kernel<NX, WPC>, bytes, smem_done); e != cudaSuccess)
+        return e;
+    constexpr int per_cta = 2 * WPC;
+    sqp_rows_kernel<NX, WPC><<<(a.ka.count + per_cta - 1) / per_cta, 32 * WPC, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+// a.ipc instances per CTA (0: 2)
 template <int NX>
 static cudaError_t launch_sqp_rows(const SqpArgs& a, cudaStream_t st)
 {
-    constexpr size_t bytes = SqpRowsSmem<NX>::BYTES;
-    static std::atomic<uint64_t> smem_done{0};
-    if (cudaError_t e = ensure_smem(sqp_rows_kernel<NX>, bytes, smem_done); e != cudaSuccess)
-        return e;
-    sqp_rows_kernel<NX><<<(a.ka.count + 1) / 2, 32, bytes, st>>>(a);
-    return cudaGetLastError();
+    switch (a.ipc) {
+        case 0:
+        case 2: return launch_sqp_rows_w<NX, 1>(a, st);
+        case 4: return launch_sqp_rows_w<NX, 2>(a, st);
+        case 8: return launch_sqp_rows_w<NX, 4>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // The scan fused SQP of small SRBD states with row-per-lane chunks: one

@@ -90,6 +90,15 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
     pl->warps = (o && o->warps) ? o->warps : pick_warps(pl->ops, pl->maxN);
     if (!warps_ok(pl->ops, pl->warps)) return PDILQR_E_INVALID_ARG;
     pl->refine = (o && o->refine) ? 1 : 0;
+    // instances per CTA: only the row-per-lane sequential SQP (one-robot
+    // SRBD, one chunk) packs several instances into a CTA
+    pl->ipc = o ? o->inst_per_cta : 0;
+    // FP64 elimination of the combines' M = I + C1 P2: the whole-body size
+    pl->m64 = (o && o->m_fp64) ? 1 : 0;
+    if (pl->m64 && !(pl->n == 36 && pl->m == 24)) return PDILQR_E_INVALID_ARG;
+    if (pl->ipc != 0 && !(pl->n == 12 && pl->m == 12 && pl->warps == 1 &&
+                          (pl->ipc == 2 || pl->ipc == 4 || pl->ipc == 8)))
+        return PDILQR_E_INVALID_ARG;
     // longest horizons first: the tail of the grid holds the short instances
     std::vector<int32_t> order(b->count);
     for (int i = 0; i < b->count; ++i) order[i] = i;
@@ -187,6 +196,7 @@ static KktArgs make_args(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s, f
     a.status = status;
     a.count = pl->count;
     a.gws = pl->gws;
+    a.m64 = pl->m64;
     a.dbg = pl->dbg;
     return a;
 }
@@ -384,6 +394,7 @@ extern "C" pdilqr_status pdilqr_solve(pdilqr_plan* pl, const pdilqr_srbd_model* 
     a.J = info->J;
     a.theta = info->theta;
     a.lqcache = pl->lqcache;
+    a.ipc = pl->ipc;
     PD_CUDA(pl->ops->sqp(a, pl->warps, (cudaStream_t)stream));
     return PDILQR_OK;
 }

@@ -587,7 +587,7 @@ extern "C" pdilqr_status pdilqr_serve_create(const pdilqr_serve_opts* o, pdilqr_
     if (sv->opts.max_N <= 0) sv->opts.max_N = 100;
     if (sv->opts.sqp_iters <= 0) sv->opts.sqp_iters = 1;
     if (sv->opts.warps == 0) sv->opts.warps = 8;
-    if (sv->opts.max_inflight > 4 || sv->opts.max_N > 4096 || sv->opts.sqp_iters > 32 ||
+    if (sv->opts.max_inflight > 16 || sv->opts.max_N > 4096 || sv->opts.sqp_iters > 32 ||
         (sv->opts.warps != 1 && sv->opts.warps != 4 && sv->opts.warps != 8 && sv->opts.warps != 16)) {
         delete sv;
         return PDILQR_E_INVALID_ARG;

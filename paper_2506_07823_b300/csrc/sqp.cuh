@@ -26,6 +26,7 @@ struct SqpArgs {
     float* alpha;                   // [count][max_iters] or null
     double *J, *theta;              // [count] or null
     float* lqcache;                 // [slots][StageL::IN] linearised-stage cache or null
+    int ipc = 0;                    // instances per CTA of the row-per-lane sequential kernel (0: 2)
 };
 
 template <int NX, int NU, int W>

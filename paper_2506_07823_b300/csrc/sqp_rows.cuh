@@ -950,23 +950,28 @@ __device__ __forceinline__ void sqp_rows_instance(const SqpArgs& a, const Grp<16
 }
 
 
-// CTAs of one warp, two instances (consecutive entries of the longest-first
-// order) per warp.  (A persistent form, a grid of the resident CTAs pulling
-// pairs from a counter, measured the same on the 4096-instance batch and 4 %
-// slower on one instance, its loop doubling the register spills; the
-// hardware's CTA scheduling over the longest-first order already balances
-// the batch, whose 2048 CTAs fit in 1.7 waves.)
-template <int NX>
-__global__ void __launch_bounds__(32, 8) sqp_rows_kernel(const __grid_constant__ SqpArgs a)
+// CTAs of WPC warps, two instances (consecutive entries of the
+// longest-first order) per warp, 2 WPC instances per CTA; the warps of a CTA
+// share nothing but the CTA (an instance's half-warp synchronises only
+// itself), so WPC sets the granularity of the hardware's CTA scheduling,
+// which the batch autotuner picks.  8 / WPC CTAs per SM at 255 registers per
+// thread (12 one-warp CTAs per SM at 168 registers spilled and were 16 %
+// slower on the 4096-instance batch).  (A persistent form, a grid of the
+// resident CTAs pulling pairs from a counter, measured the same on that
+// batch and 4 % slower on one instance, its loop doubling the register
+// spills; the hardware's CTA scheduling over the longest-first order already
+// balances the batch, whose 2048 one-warp CTAs fit in 1.7 waves.)
+template <int NX, int WPC>
+__global__ void __launch_bounds__(32 * WPC, 8 / WPC) sqp_rows_kernel(const __grid_constant__ SqpArgs a)
 {
     using SM = SqpRowsSmem<NX>;
     extern __shared__ __align__(16) float smem[];
-    const int lane = threadIdx.x & 31, h = lane >> 4;
-    const int slot = 2 * blockIdx.x + h;
-    if (slot >= a.ka.count) return;   // an odd count: the other half runs alone
+    const int lane = threadIdx.x & 31, h = lane >> 4, wp = threadIdx.x >> 5;
+    const int slot = 2 * (blockIdx.x * WPC + wp) + h;
+    if (slot >= a.ka.count) return;   // past the batch's end: this half runs nothing
     Grp<16> g{lane & 15, 0};
     g.mask = 0xffffu << (16 * h);
-    sqp_rows_instance<NX>(a, g, smem + h * SM::PER, a.ka.order ? a.ka.order[slot] : slot);
+    sqp_rows_instance<NX>(a, g, smem + (2 * wp + h) * SM::PER, a.ka.order ? a.ka.order[slot] : slot);
 }
 
 }  // namespace pdl

@@ -42,7 +42,8 @@ class _Batch(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("warps", ctypes.c_int32), ("refine", ctypes.c_int32)]
+    _fields_ = [("warps", ctypes.c_int32), ("refine", ctypes.c_int32),
+                ("inst_per_cta", ctypes.c_int32), ("m_fp64", ctypes.c_int32)]
 
 
 class _LQ(ctypes.Structure):
@@ -205,19 +206,21 @@ class Plan:
     batch hold ``N_i + 1`` slots per instance starting at ``stage_off[i]``.
     """
 
-    def __init__(self, n: int, m: int, N, stage_off, warps: int = 0, refine: bool = False):
+    def __init__(self, n: int, m: int, N, stage_off, warps: int = 0, refine: bool = False,
+                 inst_per_cta: int = 0, m_fp64: bool = False):
         self.n, self.m = int(n), int(m)
         self.N = np.ascontiguousarray(np.asarray(N, dtype=np.int32))
         self.stage_off = np.ascontiguousarray(np.asarray(stage_off, dtype=np.int64))
         self.count = int(self.N.size)
         self.total = int((self.stage_off + self.N + 1).max())
         b = _Batch(self.n, self.m, self.count, self.N.ctypes.data, self.stage_off.ctypes.data)
-        o = _Opts(int(warps), int(bool(refine)))
+        o = _Opts(int(warps), int(bool(refine)), int(inst_per_cta), int(bool(m_fp64)))
         h = _vp()
         _check(_lib.pdilqr_plan_create(ctypes.byref(b), ctypes.byref(o), ctypes.byref(h)),
                "pdilqr_plan_create")
         self._h = h
         self.warps = int(_lib.pdilqr_plan_warps(h))
+        self.inst_per_cta = int(inst_per_cta)
 
     def set_debug(self, flags: int):
         """Test switches of the plan (``DEBUG_TC_SKIP_ISSUE``,

@@ -304,3 +304,44 @@ def test_misaligned_arrays_are_rejected():
     lq["q"] = shifted[1:].reshape(base.shape)
     with pytest.raises(pdilqr.PdilqrError, match="INVALID_ARG"):
         plan.riccati_solve(lq, sd)
+
+
+@pytest.mark.parametrize("warps", [4, 8])
+def test_m_fp64_parity_ragged(warps):
+    """The scan with its combines' M = I + C1 P2 eliminated in FP64 (the
+    whole-body size): uneven horizons, policy and value function against the
+    oracle."""
+    from paper_2506_07823_b300.pdilqr import Plan
+    Ns = [1, 2, 3, 5, 16, 17, 50, 100]
+    insts, packed, Nv, off, s = make_batch(36, 24, Ns, seed=3624)
+    plan = Plan(36, 24, Nv, off, warps=warps, m_fp64=True)
+    lq, sd = to_dev(packed, s, False)
+    out = plan.kkt_scan_solve(lq, sd, want_policy=True)
+    torch.cuda.synchronize()
+    check_parity(insts, Nv, off, out, s, False, policy=True)
+
+
+def test_m_fp64_whole_body_workload():
+    """The whole-body-sized recipe through the FP64-M scan, unrefined and
+    refined, within the stated tolerances of the oracle."""
+    cfg = synth.LQ_WB
+    insts, packed, Nv, off, s = make_batch(36, 24, [100, 100, 37], seed=4000, rho=cfg["rho"],
+                                           b_std=cfg["b_std"], q_kind=cfg["q_kind"], r_w=cfg["r_w"])
+    from paper_2506_07823_b300.pdilqr import Plan, backward_error
+    lq, sd = to_dev(packed, s, False)
+    for refine in (False, True):
+        plan = Plan(36, 24, Nv, off, m_fp64=True, refine=refine)
+        out = plan.kkt_scan_solve(lq, sd, want_resid=True)
+        torch.cuda.synchronize()
+        check_parity(insts, Nv, off, out, s, False)
+        if refine:
+            assert float(backward_error(out["resid"]).max()) <= BWD_TOL
+
+
+def test_m_fp64_rejected_elsewhere():
+    """The FP64 elimination of M exists at (n, m) = (36, 24) only."""
+    from paper_2506_07823_b300 import pdilqr
+    for n, m in ((12, 12), (24, 24), (4, 2)):
+        with pytest.raises(pdilqr.PdilqrError) as e:
+            pdilqr.Plan(n, m, [10, 20], [0, 11], m_fp64=True)
+        assert e.value.code == pdilqr.E_INVALID_ARG

@@ -314,17 +314,19 @@ def test_tensor_core_wait_timeout_status():
     assert rel(d["x"].double().cpu().numpy(), xr) <= REL_TOL
 
 
-def test_sqp_sequential_odd_batch():
+@pytest.mark.parametrize("ipc", [2, 4, 8])
+def test_sqp_sequential_odd_batch(ipc):
     """The two-instances-per-warp sequential solver on an odd batch (the last
-    warp runs one instance) with horizons 1 (degenerate) to 100, replaying
-    the oracle's step sizes."""
+    warp runs one instance; at 4 and 8 instances per CTA whole warps of the
+    last CTA run none) with horizons 1 (degenerate) to 100, replaying the
+    oracle's step sizes."""
     from paper_2506_07823_b300 import pdilqr
     iters = 4
     insts, packed, Nv, off, x0 = srbd_case(5, 91, [1, 100, 13, 2, 50])
     prm = synth.srbd_params()
     refs = [run_oracle(prm, pr, iters) for pr in insts]
     d = dev(packed)
-    plan = pdilqr.Plan(12, 12, Nv, off, warps=1)
+    plan = pdilqr.Plan(12, 12, Nv, off, warps=1, inst_per_cta=ipc)
     replay = torch.tensor(np.stack([r[3]["alpha"] for r in refs]).astype(np.float32), device="cuda")
     info = plan.solve(pdilqr.srbd_model(prm), torch.tensor(x0, dtype=torch.float32, device="cuda"),
                       d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
@@ -374,3 +376,63 @@ def test_captured_solve_replays_like_a_direct_solve():
                 assert torch.equal(d[k], ref[k]), (warps, k)
             assert torch.equal(info["status"], want["status"])
             assert torch.equal(info["iters"], want["iters"])
+
+
+def test_instances_per_cta_same_result():
+    """Packing 2, 4 or 8 instances into a CTA changes only which CTA runs an
+    instance: every instance's iterate is bit-identical across the three."""
+    from paper_2506_07823_b300 import pdilqr
+    insts, packed, Nv, off, x0 = srbd_case(11, 7, [25, 50, 75, 100])
+    md = pdilqr.srbd_model(synth.srbd_params())
+    x0d = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    outs = []
+    for ipc in (2, 4, 8):
+        d = dev(packed)
+        plan = pdilqr.Plan(12, 12, Nv, off, warps=1, inst_per_cta=ipc)
+        info = plan.solve(md, x0d, d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                          max_iters=3)
+        torch.cuda.synchronize()
+        outs.append((d["x"].clone(), d["u"].clone(), d["lam"].clone(), info["status"].clone()))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
+
+
+def test_instances_per_cta_rejected_elsewhere():
+    """Only the one-robot sequential solver packs several instances per CTA;
+    other solvers, sizes and counts are invalid arguments."""
+    from paper_2506_07823_b300 import pdilqr
+    for n, warps, ipc in ((12, 4, 4), (12, 1, 3), (12, 1, 16), (24, 1, 2)):
+        with pytest.raises(pdilqr.PdilqrError) as e:
+            pdilqr.Plan(n, n, [10, 20], [0, 11], warps=warps, inst_per_cta=ipc)
+        assert e.value.code == pdilqr.E_INVALID_ARG
+
+
+def test_autotune_picks_a_timed_configuration():
+    """The batch autotuner times every configuration of a one-robot batch
+    and returns the plan of the fastest; its solve matches a plain plan's."""
+    from paper_2506_07823_b300 import autotune, pdilqr
+    insts, packed, Nv, off, x0 = srbd_case(16, 3, [25, 50, 75, 100])
+    md = pdilqr.srbd_model(synth.srbd_params())
+    x0d = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    d = dev(packed)
+    base = {k: v.clone() for k, v in d.items()}
+
+    def reset():
+        for k in ("x", "u", "lam"):
+            d[k].copy_(base[k])
+
+    def solve(p):
+        return p.solve(md, x0d, d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                       max_iters=2)
+    plan, times = autotune.autotune_sqp(torch, 12, 12, Nv, off, solve, reset=reset, reps=1)
+    assert set(times) == {autotune.label(w, i) for w, i in autotune.candidates(12, 12)}
+    assert autotune.label(plan.warps, plan.inst_per_cta) == min(times, key=times.get)
+    reset()
+    solve(plan)
+    torch.cuda.synchronize()
+    got = d["x"].clone()
+    reset()
+    solve(pdilqr.Plan(12, 12, Nv, off, warps=plan.warps))
+    torch.cuda.synchronize()
+    assert rel(got.double().cpu().numpy(), d["x"].double().cpu().numpy()) <= REL_TOL
