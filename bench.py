@@ -456,7 +456,8 @@ def run_gpu(args):
                                      "and 16 robots (n = 12 R)",
                 "continuous_batching_full_mix": measure_serving(pdilqr, args, args.mix_seconds,
                                                                 args.serve_rate, 1024, 8,
-                                                                args.mix_streams, mix="full")}
+                                                                args.mix_streams, mix="full",
+                                                                large_cta_budget=args.mix_large_ctas)}
         e2e = measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args)
         sweep = measure_sweep(torch, pdilqr, dev, stream, args.sweep_reps) if args.sweep_reps > 0 else None
         cpu = None
@@ -813,7 +814,7 @@ def client_robots(c: int, mix: str) -> int:
 
 
 def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, warps: int,
-                    inflight: int, seed: int = 0, mix: str = "pair"):
+                    inflight: int, seed: int = 0, mix: str = "pair", large_cta_budget: int = 0):
     """Poisson arrivals at ``rate`` requests/s for ``seconds``: each request is
     one real-time SQP iteration of a client's MPC problem (N = 50; robots per
     client as ``client_robots``, several robots coupled by the formation
@@ -824,7 +825,8 @@ def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, w
     classes = {r: synth.srbd_params(r) for r in (1, 2, 4, 8, 16)}
     srv = pdilqr.Server(prm, hbm_budget_bytes=(1 << 30) if mix == "pair" else (16 << 30),
                         max_batch=max_batch, max_inflight=inflight, max_N=50, sqp_iters=1,
-                        warps=warps, class_params=classes if mix != "pair" else None)
+                        warps=warps, class_params=classes if mix != "pair" else None,
+                        large_cta_budget=large_cta_budget)
     # a client's ticks run one after another (each warm-starts the next), so
     # the full mix spreads the offered rate over more clients
     n_clients = 256 if mix == "pair" else 1024
@@ -888,7 +890,7 @@ def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, w
     out = {"offered_per_s": rate, "requests": k, "solves_per_s": len(lat) / (t1 - t0),
            "p50_ms": pct(lat, 50) / 1e3, "p99_ms": pct(lat, 99) / 1e3,
            "mean_batch": st["mean_batch"], "max_batch": max_batch, "warps": warps,
-           "streams": inflight}
+           "streams": inflight, "large_cta_budget": large_cta_budget}
     if mix != "pair":
         out["by_robots"] = {str(r): {"requests": len(v), "p50_ms": pct(v, 50) / 1e3,
                                      "p99_ms": pct(v, 99) / 1e3}
@@ -1037,6 +1039,10 @@ def main():
     ap.add_argument("--mix-seconds", type=float, default=60.0,
                     help="duration of the full robot-count mix (0 skips it with the others when "
                          "--serve-seconds is 0)")
+    ap.add_argument("--mix-large-ctas", type=int, default=0,
+                    help="large_cta_budget of the full-mix server: most instances of 4+ robots "
+                         "in flight (0: no budget; with 8 streams a budget of 32 or 64 did not "
+                         "bring the small classes back to their 4-stream latency)")
     ap.add_argument("--mix-streams", type=int, default=4,
                     help="batches in flight (streams) of the full-mix server, 1..16 (8 measured "
                          "worse than 4: large-class batches then occupy every SM and the "

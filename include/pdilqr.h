@@ -366,6 +366,12 @@ typedef struct {
                                /* NULL: `model` for every class                    */
     int64_t hbm_reserve_bytes; /* device memory left free when a size class's     */
                                /* batch workspace is first needed (0: 256 MiB)    */
+    int32_t large_cta_budget;  /* most instances of the classes of 4+ robots in   */
+                               /* flight at once (each runs on one CTA for tens  */
+                               /* of milliseconds); a large batch is launched    */
+                               /* only while the budget has room and is cut to   */
+                               /* it, so that the SMs it leaves serve the small  */
+                               /* classes.  0: no budget (streams limit alone)   */
 } pdilqr_serve_opts;
 
 typedef struct {

@@ -498,9 +498,15 @@ void worker_loop(pdilqr_server* sv)
             if (!sl.busy) { free_slot = &sl; break; }
         // the oldest request whose client is idle fixes the size class (a large
         // class only while it leaves a stream for the small ones)
-        int large_busy = 0;
-        for (const Slot& sl : sv->slots) large_busy += (sl.busy && sl.cls >= kLargeClass) ? 1 : 0;
-        const bool large_ok = sv->opts.max_inflight < 2 || large_busy < sv->opts.max_inflight - 1;
+        int large_busy = 0, large_ctas = 0;
+        for (const Slot& sl : sv->slots)
+            if (sl.busy && sl.cls >= kLargeClass) {
+                large_busy += 1;
+                large_ctas += sl.count;
+            }
+        const int budget = sv->opts.large_cta_budget;
+        const bool large_ok = (sv->opts.max_inflight < 2 || large_busy < sv->opts.max_inflight - 1) &&
+                              (budget <= 0 || large_ctas < budget);
         int cls = -1;
         for (const Request& q : sv->pending) {
             auto c = sv->clients.find(q.client);
@@ -516,7 +522,8 @@ void worker_loop(pdilqr_server* sv)
             }
             std::vector<Request> reqs;
             std::vector<Client*> cl;
-            const int cap = class_batch(sv, cls);
+            int cap = class_batch(sv, cls);
+            if (cls >= kLargeClass && budget > 0) cap = std::min(cap, budget - large_ctas);
             for (auto it = sv->pending.begin();
                  it != sv->pending.end() && (int)reqs.size() < cap;) {
                 auto cit = sv->clients.find(it->client);
@@ -587,7 +594,8 @@ extern "C" pdilqr_status pdilqr_serve_create(const pdilqr_serve_opts* o, pdilqr_
     if (sv->opts.max_N <= 0) sv->opts.max_N = 100;
     if (sv->opts.sqp_iters <= 0) sv->opts.sqp_iters = 1;
     if (sv->opts.warps == 0) sv->opts.warps = 8;
-    if (sv->opts.max_inflight > 16 || sv->opts.max_N > 4096 || sv->opts.sqp_iters > 32 ||
+    if (sv->opts.max_inflight > 16 || sv->opts.large_cta_budget < 0 || sv->opts.max_N > 4096 ||
+        sv->opts.sqp_iters > 32 ||
         (sv->opts.warps != 1 && sv->opts.warps != 4 && sv->opts.warps != 8 && sv->opts.warps != 16)) {
         delete sv;
         return PDILQR_E_INVALID_ARG;

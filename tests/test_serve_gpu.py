@@ -234,3 +234,31 @@ def test_large_classes_match_oracle():
                    np.zeros((11, 36), np.float32), np.zeros((11, 12), np.uint8))
     assert e.value.code == pdilqr.E_INVALID_ARG
     srv.close()
+
+
+def test_large_cta_budget_splits_batches():
+    """With a budget of two large-class instances in flight, six four-robot
+    requests that arrive together run as batches of at most two, each result
+    still the oracle's; a negative budget is an invalid argument."""
+    from paper_2506_07823_b300 import pdilqr
+    prm4 = synth.srbd_params(4)
+    srv = make_server(prm4, class_params={4: prm4}, max_N=12, max_inflight=4, large_cta_budget=2)
+    r32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    N = 8
+    probs = {c: synth.srbd_problem(N, seed=3000 + c, nrob=4) for c in range(60, 66)}
+    tickets = {c: srv.submit(c, 4, N, p["x0hat"].astype(np.float32), p["xref"], p["uref"],
+                             p["contact"]) for c, p in probs.items()}
+    for c, tk in tickets.items():
+        res = srv.poll(tk, n=48, N=N, timeout_us=60_000_000)
+        assert res["status"] in (0, 8), (c, res["status"])
+        p = probs[c]
+        x, u, lam, info = oracle.srbd_sqp(prm4, r32(p["x0hat"]), np.tile(r32(p["x0hat"]), (N + 1, 1)),
+                                          r32(p["uref"]), np.zeros((N + 1, 48)), r32(p["xref"]),
+                                          r32(p["uref"]), p["contact"], max_iters=1)
+        assert rel(res["x"], x) <= REL_TOL, (c, rel(res["x"], x))
+    st = srv.stats()
+    assert st["completed"] == 6 and st["batches"] >= 3, st
+    srv.close()
+    with pytest.raises(pdilqr.PdilqrError) as e:
+        make_server(large_cta_budget=-1)
+    assert e.value.code == pdilqr.E_INVALID_ARG
