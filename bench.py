@@ -683,6 +683,49 @@ def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, plans,
     return {"latency": lat, "comparators": comp}
 
 
+def measure_large_state_lq(torch, pdilqr, oracle, dev, stream, args):
+    """One instance's LQ KKT solve at the centralised multi-robot sizes (n = m =
+    12 R for R = 4, 8, 16; N = 50; the whole-body LTV recipe at that size) by
+    the sequential recursion (one CTA), the scan over 4 chunks inside one CTA,
+    and the split scan (16 chunks on 16 CTAs), unrefined and with one
+    refinement step: p50 / p99 over direct calls (CUDA events), and each
+    result's error against the FP64 oracle."""
+    rows = []
+    reps = max(5, min(args.latency_reps, 20))
+    for R in (4, 8, 16):
+        n = 12 * R
+        inst = synth.ltv_lq(n, n, 50, seed=500 + R, rho=0.98, b_std=0.2, q_kind="llt", r_w=0.01)
+        pk, Nv1, off1 = synth.pack([inst], synth.LQ_KEYS)
+        lq1 = {k: torch.tensor(np.asarray(v, np.float32), device=dev) for k, v in pk.items()}
+        lq1["S"] = None
+        s1 = torch.tensor(np.asarray(inst["s"][None], np.float32), device=dev)
+        r32 = {k: np.asarray(inst[k], np.float32).astype(np.float64) for k in synth.LQ_KEYS}
+        ref = oracle.riccati_solve(r32, np.asarray(inst["s"], np.float32).astype(np.float64))
+        row = {"robots": R, "n": n, "N": 50}
+        for name, kw in (("sequential", dict(warps=1)), ("scan_one_cta", dict(warps=4)),
+                         ("scan_split", dict(warps=16, split=True)),
+                         ("sequential_refined", dict(warps=1, refine=True)),
+                         ("scan_split_refined", dict(warps=16, split=True, refine=True))):
+            p1 = pdilqr.Plan(n, n, Nv1, off1, **kw)
+            o1 = p1.alloc_out(device=dev)
+            p1.kkt_scan_solve(lq1, s1, out=o1)
+            torch.cuda.synchronize()
+            t = event_times(torch, lambda: p1.kkt_scan_solve(lq1, s1, out=o1), reps, stream)
+            err = 0.0
+            for k, n_slots in (("dx", 51), ("du", 50), ("dlam", 51)):
+                got = o1[k].double().cpu().numpy()[:n_slots]
+                want = ref[k][:n_slots]
+                err = max(err, float(np.abs(got - want).max() / np.abs(want).max()))
+            row[name] = {"p50_ms": pct(t, 50), "p99_ms": pct(t, 99), "ctas": p1.warps if kw.get("split") else 1,
+                         "status": int(o1["status"][0].item()), "max_rel_error_vs_oracle": err}
+            p1.close()
+        row["split_speedup_vs_sequential"] = row["sequential"]["p50_ms"] / row["scan_split"]["p50_ms"]
+        row["split_speedup_vs_sequential_refined"] = (row["sequential_refined"]["p50_ms"] /
+                                                      row["scan_split_refined"]["p50_ms"])
+        rows.append(row)
+    return rows
+
+
 def measure_lq_workloads(torch, pdilqr, dev, stream, args):
     """LQ KKT solves alone: the whole-body-sized batch (n = 36, m = 24,
     N = 100, 1024 instances; 128 distinct instances replicated eight times)
@@ -767,6 +810,7 @@ def measure_lq_workloads(torch, pdilqr, dev, stream, args):
         t = event_times(torch, g.replay, args.latency_reps, stream)
         single[name] = {"p50_us": pct(t, 50) * 1e3, "p99_us": pct(t, 99) * 1e3}
     out["single_lqr_n4_N16"] = single
+    out["large_state_lq"] = measure_large_state_lq(torch, pdilqr, oracle, dev, stream, args)
     return out
 
 

@@ -98,6 +98,16 @@ typedef struct {
                         /* FP32 entries widened once, results rounded back); */
                         /* 0: in FP32.  Only (n, m) = (36, 24); other sizes  */
                         /* require 0.  The Riccati solver is unaffected.     */
+    int32_t split;      /* 1: the scan's horizon chunks run on separate CTAs */
+                        /* (one per chunk, warps = 8 or 16, 0 picks 16), so  */
+                        /* that one instance spreads over that many SMs;    */
+                        /* the CTAs of an instance meet at bounded barriers */
+                        /* between the scan's phases (cooperative launch).  */
+                        /* Sizes with n >= 48 only; the LQ solves           */
+                        /* (pdilqr_kkt_scan_solve) use it, the fused SQP    */
+                        /* (pdilqr_solve) does not.  Errors: INVALID_ARG for */
+                        /* other sizes or warps; a launch whose warps x     */
+                        /* count CTAs cannot all be resident fails (CUDA).  */
 } pdilqr_opts;
 
 typedef struct pdilqr_plan pdilqr_plan;

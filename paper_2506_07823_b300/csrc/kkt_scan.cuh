@@ -65,6 +65,7 @@ struct KktArgs {
     int dbg;                                     // test switches (PDILQR_DEBUG_*), normally 0
     int m64 = 0;                                 // 1: the combines eliminate M = I + C1 P2
                                                  // in FP64 (n = 36; gj_solve_f64)
+    unsigned* sbar = nullptr;                    // [count] phase counters of the split scan
 };
 
 // ------------------------------------------------------------------ layouts
@@ -694,6 +695,33 @@ struct UseTc {
     static constexpr uint32_t cols = (uint32_t)tc_cols(R);
 };
 
+// Barrier of the W CTAs that share one instance in the split scan (one CTA
+// per horizon chunk, launched cooperatively so that all of them are
+// resident): every CTA adds one to the instance's counter and waits until it
+// reaches `target` (phase number x W).  The writes of all threads of a CTA
+// before the barrier are published by thread 0's fence before its arrival,
+// and the fence after the wait orders the reads that follow.  The wait is
+// bounded (2 s by the global timer): a barrier that does not complete sets
+// `late` (thread 0's) and lets the CTA go on, so that the kernel always ends.
+__device__ __forceinline__ void split_barrier(unsigned* cnt, unsigned target, int& late)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(cnt, 1u);
+        const uint64_t t0 = globaltimer_ns();
+        while (*(volatile unsigned*)cnt < target) {
+            if (globaltimer_ns() - t0 > 2000000000ull) {
+                late = 1;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
 // The scan solve of one instance by the CTA (all threads must call it).
 // src provides the LQ stages; s_inst points to this instance's dx_0 (global
 // or shared memory).  Returns the instance status (uniform over the CTA).
@@ -701,23 +729,37 @@ struct UseTc {
 // The horizon is split into W chunks, each owned by a unit of UW warps
 // (NT = 32 UW threads: one warp for small states, several for large ones,
 // synchronised by a named barrier per unit).
-template <int NX, int NU, int W, int UW, class Src>
+//
+// SPLIT: the chunks run on separate CTAs (chunk = blockIdx.x, one unit per
+// CTA, launched cooperatively), smem is the instance's work area in global
+// memory, tiles / factors / tc belong to this CTA's single unit, and the
+// barriers between phases are split_barrier on the instance's counter sbar.
+template <int NX, int NU, int W, int UW, class Src, bool SPLIT = false>
 __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
                           const float* s_inst, float* smem, float* tiles = nullptr,
-                          float* factors = nullptr, TcCtx* tc = nullptr)
+                          float* factors = nullptr, TcCtx* tc = nullptr, unsigned* sbar = nullptr)
 {
     using SM = ScanSmem<NX, NU, W>;
     using E = ElemL<NX>;
     constexpr int NT = 32 * UW;
-    const int warp = threadIdx.x / NT;     // the unit (chunk) of this thread
-    using UF = UnitFactor<NU, W, UW>;
+    constexpr int WU = SPLIT ? 1 : W;      // units per CTA
+    const int warp = SPLIT ? (int)blockIdx.x : (int)(threadIdx.x / NT);   // the chunk
+    const int unit = SPLIT ? 0 : warp;     // the unit within this CTA
+    using UF = UnitFactor<NU, WU, UW>;
     // factor buffers exist for this configuration (the caller passes them
     // whenever they fit); the shared-memory solves are compiled only then
-    constexpr bool FAC = UF::FLOATS > 0 && UF::BYTES + UnitTiles<W, UW>::BYTES + 1024 <= kSmemCta;
-    const Grp<NT> g{(int)(threadIdx.x % NT), 1 + warp,
-                    tiles ? tiles + warp * TileBuf::FLOATS : nullptr,
-                    factors ? factors + (size_t)warp * UF::FLOATS : nullptr, factors ? UF::FLOATS : 0,
+    constexpr bool FAC = UF::FLOATS > 0 && UF::BYTES + UnitTiles<WU, UW>::BYTES + 1024 <= kSmemCta;
+    const Grp<NT> g{(int)(threadIdx.x % NT), 1 + unit,
+                    tiles ? tiles + unit * TileBuf::FLOATS : nullptr,
+                    factors ? factors + (size_t)unit * UF::FLOATS : nullptr, factors ? UF::FLOATS : 0,
                     tc};
+    // barrier between phases: the CTA, or the instance's CTAs in split mode
+    int late = 0;             // thread 0: a split barrier that ran out
+    unsigned sb_phase = 0;
+    auto phase_sync = [&]() {
+        if constexpr (SPLIT) split_barrier(sbar, (++sb_phase) * (unsigned)gridDim.x, late);
+        else __syncthreads();
+    };
     const int S = N + 1;
     const int Weff = W < S ? W : S;
     const bool has_S = src.has_S();
@@ -727,7 +769,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     float* xs = smem + SM::SLOTS + W * SM::PRIV;       // [W][NX] chunk start states
     int* st_word = reinterpret_cast<int*>(xs + SM::XS);
     if (threadIdx.x == 0) st_word[0] = ST_OK;
-    __syncthreads();
+    phase_sync();
 
     const int k0 = chunk_start(warp, Weff, S);
     const int k1 = chunk_start(warp + 1, Weff, S);
@@ -782,7 +824,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         }
         copy<NX * NX + NX, 1, false, NT>(g, slots + warp * SM::SLOT + E::P, 1, v0, 1);
     }
-    __syncthreads();
+    phase_sync();
 
     // ---- phase 2: suffix scan over the chunk aggregates, items 0..J-1 of
     // chunks 1..Weff-1 (the last is a value function).  The levels alternate
@@ -816,7 +858,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
                     copy<NX * NX + NX, 1, false, NT>(g, out + E::P, 1, e1 + E::P, 1);
                 }
             }
-            __syncthreads();
+            phase_sync();
             in_b = !in_b;
         }
     }
@@ -835,7 +877,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         const float* vb = in_b ? bufB + (warp + 1) * SM::PRIV : bufA + (warp + 1) * SM::SLOT;
         copy<NX * NX + NX, 1, false, NT, false>(g, v0, 1, vb + E::P, 1);
     }
-    __syncthreads();
+    phase_sync();
     if (active && !last) {
         float* scr = v1 + SM::VF;
         fill<NX, NX, NT, false>(g, psiA, NX, 0.f, 1.f);
@@ -861,7 +903,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         if (psiA != slots + warp * SM::SLOT) copy<NX * NX, 1, false, NT>(g, slots + warp * SM::SLOT, 1, psiA, 1);
     }
     if (bad != ST_OK && g.t == 0) atomicMax(st_word, bad);
-    __syncthreads();
+    phase_sync();
 
     // ---- phase 4: trajectory scan.  Chunk start states from dx_0 through the
     // chunk maps, then every chunk rolls out dx, du, dlam.
@@ -875,7 +917,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
             mv<NX, NX, false, NT>(g, xs + (w + 1) * round4(NX), Psi, NX, xs + w * round4(NX), psv);
         }
     }
-    __syncthreads();
+    phase_sync();
     if (active) {
         float* x = priv;                 // reuse the private area
         float* xn = priv + round4(NX);
@@ -884,11 +926,16 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
         g.sync();
         if (!rollout_chunk<NX, NU, NT>(g, x, xn, rb, a, off, N, k0, k1)) atomicMax(st_word, ST_NONFINITE);
     }
-    __syncthreads();
+    phase_sync();
+    if constexpr (SPLIT) {
+        // every CTA's timeouts (barrier or tensor-core wait) reach the status
+        if (threadIdx.x == 0 && (late || (tc && tc->failed))) atomicMax(st_word, ST_TIMEOUT);
+        phase_sync();
+    }
     int status = st_word[0];
     // a tensor-core product whose bounded wait ran out (uniform over the CTA)
     if (tc && tc->failed) status = ST_TIMEOUT;
-    __syncthreads();
+    phase_sync();
     return status;
 }
 
@@ -938,6 +985,42 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     if (threadIdx.x == 0) a.status[inst] = st;
 }
 
+
+// The split scan (Sec. II-D over several SMs): one CTA per horizon chunk
+// (blockIdx.x) and one grid row per instance (blockIdx.y, longest first),
+// launched cooperatively so that the W CTAs of an instance are resident
+// together and meet at the bounded phase barriers (a.sbar[row], zeroed
+// before the launch).  Each CTA is one unit of UW warps with its own tile
+// buffer, factor buffer and, where the one-chunk kernels have them,
+// tensor-core products; the instance's chunk aggregates and work areas live
+// in the global workspace (ScanSmem<NX, NU, W>::TOTAL floats per instance).
+template <int NX, int NU, int W, int UW>
+__global__ void __launch_bounds__(32 * UW, 1) kkt_scan_split_kernel(const __grid_constant__ KktArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    using TL = UnitTiles<1, UW>;
+    using UF = UnitFactor<NU, 1, UW>;
+    if ((int)blockIdx.y >= a.count) return;   // a whole grid row: no barrier waits on it
+    const int inst = a.order ? a.order[blockIdx.y] : (int)blockIdx.y;
+    const LqSource src(a);
+    float* work = a.gws + (int64_t)blockIdx.y * ScanSmem<NX, NU, W>::TOTAL;
+    float* tiles = TL::fit(0) ? smem + TL::at(0) / sizeof(float) : nullptr;
+    const size_t fbase = TL::total(0);
+    float* factors = UF::fit(fbase) ? smem + UF::at(fbase) / sizeof(float) : nullptr;
+    TcCtx* tc = nullptr;
+    if constexpr (UseTc<NX, NU, 1, UW>::value) {
+        __shared__ TcCtx tcx;
+        if (factors) {
+            tc_setup(&tcx, UseTc<NX, NU, 1, UW>::cols, (a.dbg & PDILQR_DEBUG_TC_SKIP_ISSUE) != 0);
+            tc = &tcx;
+        }
+    }
+    const int st = scan_solve<NX, NU, W, UW, LqSource, true>(src, a, a.N[inst], a.off[inst],
+                                                             a.s + (int64_t)inst * NX, work, tiles,
+                                                             factors, tc, a.sbar + blockIdx.y);
+    if (tc) tc_teardown(tc);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.status[inst] = st;
+}
 
 // Scan solve for the allocation-free entry point: the batch tables come from
 // the caller, so every instance's slot range is checked against the scratch

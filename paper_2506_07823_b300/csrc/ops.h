@@ -33,6 +33,11 @@ struct SizeOps {
     size_t (*scan_gws_floats)(int warps);
     int unit_warps;        // warps per horizon chunk; warps x unit_warps <= 32
     size_t lin_ws_floats;  // global workspace of the standalone linearisation (0: none)
+    // the split scan (one CTA per horizon chunk, W = 8 or 16; sizes whose
+    // chunks are 8-warp units) and its global workspace per instance; null /
+    // 0 for other sizes
+    cudaError_t (*scan_split)(const KktArgs&, int warps, cudaStream_t);
+    size_t (*scan_split_gws_floats)(int warps);
 };
 
 // Warp counts (horizon chunks) a size supports: 1, 4, 8 or 16 within the

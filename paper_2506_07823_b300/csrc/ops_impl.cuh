@@ -264,6 +264,61 @@ static cudaError_t launch_sqp_w(const SqpArgs& a, cudaStream_t st)
     }
 }
 
+// The split scan: W CTAs per instance (one per horizon chunk), launched
+// cooperatively after the instances' phase counters are zeroed.  The launch
+// is refused (cudaErrorCooperativeLaunchTooLarge) when the W x count CTAs
+// cannot all be resident at once, which the phase barriers need.
+template <int NX, int NU, int W>
+static cudaError_t launch_scan_split_w(const KktArgs& a, cudaStream_t st)
+{
+    constexpr int UW = UnitWarps<NX>::value;
+    if constexpr (UW < 8) {
+        return cudaErrorInvalidConfiguration;
+    } else {
+        constexpr size_t tb = UnitTiles<1, UW>::total(0);
+        constexpr size_t bytes = UnitFactor<NU, 1, UW>::total(tb);
+        if (!a.gws || !a.sbar || a.count < 1) return cudaErrorInvalidValue;
+        auto kern = kkt_scan_split_kernel<NX, NU, W, UW>;
+        static std::atomic<uint64_t> smem_done{0};
+        if (cudaError_t e = ensure_smem(kern, bytes, smem_done); e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaError_t e = cudaGetDevice(&dev); e != cudaSuccess) return e;
+        if (cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev); e != cudaSuccess)
+            return e;
+        if (cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * UW, bytes);
+            e != cudaSuccess)
+            return e;
+        if ((int64_t)W * a.count > (int64_t)per_sm * sms) return cudaErrorCooperativeLaunchTooLarge;
+        if (cudaError_t e = cudaMemsetAsync(a.sbar, 0, sizeof(unsigned) * a.count, st); e != cudaSuccess)
+            return e;
+        KktArgs b = a;
+        void* args[] = {(void*)&b};
+        return cudaLaunchCooperativeKernel((const void*)kern, dim3(W, a.count), dim3(32 * UW), args,
+                                           bytes, st);
+    }
+}
+
+template <int NX, int NU>
+static cudaError_t launch_scan_split(const KktArgs& a, int warps, cudaStream_t st)
+{
+    switch (warps) {
+        case 8: return launch_scan_split_w<NX, NU, 8>(a, st);
+        case 16: return launch_scan_split_w<NX, NU, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NX, int NU>
+static size_t scan_split_gws_floats(int warps)
+{
+    if (UnitWarps<NX>::value < 8) return 0;
+    switch (warps) {
+        case 8: return ScanSmem<NX, NU, 8>::TOTAL;
+        case 16: return ScanSmem<NX, NU, 16>::TOTAL;
+        default: return 0;
+    }
+}
+
 // The one-chunk (sequential recursion) fused SQP of small SRBD states: the
 // row-per-lane kernel, two instances per warp, WPC warps per CTA.
 template <int NX, int WPC>
@@ -373,6 +428,10 @@ static SizeOps make_ops()
     o.lq_stage_floats = StageL<NX, NU>::IN;
     o.scan_gws_floats = scan_gws_floats<NX, NU>;
     o.unit_warps = UnitWarps<NX>::value;
+    if constexpr (UnitWarps<NX>::value == 8) {
+        o.scan_split = launch_scan_split<NX, NU>;
+        o.scan_split_gws_floats = scan_split_gws_floats<NX, NU>;
+    }
     if constexpr (SRBD) {
         o.linearize = launch_linearize<NX, NU>;
         o.lin_ws_floats = lin_ws_floats<NX, NU>();

@@ -87,8 +87,16 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
         const int pa = by_off[i - 1], pb = by_off[i];
         if (hoff[pa] + hN[pa] + 1 > hoff[pb]) return PDILQR_E_INVALID_ARG;
     }
-    pl->warps = (o && o->warps) ? o->warps : pick_warps(pl->ops, pl->maxN);
-    if (!warps_ok(pl->ops, pl->warps)) return PDILQR_E_INVALID_ARG;
+    pl->split = (o && o->split) ? 1 : 0;
+    if (pl->split) {
+        // chunks on separate CTAs: sizes with 8-warp units, 8 or 16 chunks
+        if (!pl->ops->scan_split) return PDILQR_E_INVALID_ARG;
+        pl->warps = (o && o->warps) ? o->warps : 16;
+        if (pl->warps != 8 && pl->warps != 16) return PDILQR_E_INVALID_ARG;
+    } else {
+        pl->warps = (o && o->warps) ? o->warps : pick_warps(pl->ops, pl->maxN);
+        if (!warps_ok(pl->ops, pl->warps)) return PDILQR_E_INVALID_ARG;
+    }
     pl->refine = (o && o->refine) ? 1 : 0;
     // instances per CTA: only the row-per-lane sequential SQP (one-robot
     // SRBD, one chunk) packs several instances into a CTA
@@ -128,9 +136,14 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
     PD_CUDA(pl->alloc(&pl->ddu, T * m));
     PD_CUDA(pl->alloc(&pl->ddl, T * n));
     // linearised-stage cache of the fused SQP (the one-chunk sweep linearises once)
-    if (pl->ops->sqp && pl->warps > 1)
+    if (pl->ops->sqp && pl->warps > 1 && !pl->split)
         PD_CUDA(pl->alloc(&pl->lqcache, T * (size_t)pl->ops->lq_stage_floats));
-    if (const size_t gw = pl->ops->scan_gws_floats(pl->warps)) PD_CUDA(pl->alloc(&pl->gws, C * gw));
+    if (pl->split) {
+        PD_CUDA(pl->alloc(&pl->gws, C * pl->ops->scan_split_gws_floats(pl->warps)));
+        PD_CUDA(pl->alloc(&pl->sbar, C));
+    } else if (const size_t gw = pl->ops->scan_gws_floats(pl->warps)) {
+        PD_CUDA(pl->alloc(&pl->gws, C * gw));
+    }
     if (pl->ops->lin_ws_floats) PD_CUDA(pl->alloc(&pl->lin_ws, pl->ops->lin_ws_floats));
     PD_CUDA(cudaMemcpy(pl->dN, hN.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(pl->doff, hoff.data(), C * sizeof(int64_t), cudaMemcpyHostToDevice));
@@ -197,6 +210,7 @@ static KktArgs make_args(pdilqr_plan* pl, const pdilqr_lq* lq, const float* s, f
     a.count = pl->count;
     a.gws = pl->gws;
     a.m64 = pl->m64;
+    a.sbar = pl->sbar;
     a.dbg = pl->dbg;
     return a;
 }
@@ -257,7 +271,8 @@ static pdilqr_status solve_common(pdilqr_plan* pl, const pdilqr_lq* lq, const fl
         return PDILQR_E_INVALID_ARG;
     if (scan && pl->ops->scan_smem(pl->warps) > kSmemMax && !pl->gws) return PDILQR_E_INVALID_ARG;
     auto run = [&](const KktArgs& a) -> cudaError_t {
-        return scan ? pl->ops->scan(a, pl->warps, st) : pl->ops->riccati(a, st);
+        if (!scan) return pl->ops->riccati(a, st);
+        return pl->split ? pl->ops->scan_split(a, pl->warps, st) : pl->ops->scan(a, pl->warps, st);
     };
     KktArgs a = make_args(pl, lq, s, out->dx, out->du, out->dlam, out->K, out->k, out->P,
                           out->p, out->status);

@@ -11,6 +11,8 @@ struct pdilqr_plan {
     int n = 0, m = 0, count = 0, warps = 0, refine = 0, maxN = 0;
     int ipc = 0;         // instances per CTA of the row-per-lane sequential SQP (0: the solver's own)
     int m64 = 0;         // 1: FP64 elimination of the scan combines' M (n = 36)
+    int split = 0;       // 1: the scan's chunks on separate CTAs (kkt_scan_split_kernel)
+    unsigned* sbar = nullptr;  // [count] phase counters of the split scan
     int64_t total = 0;
     const pdl::SizeOps* ops = nullptr;
     std::vector<void*> allocs;

@@ -43,7 +43,8 @@ class _Batch(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_int32), ("refine", ctypes.c_int32),
-                ("inst_per_cta", ctypes.c_int32), ("m_fp64", ctypes.c_int32)]
+                ("inst_per_cta", ctypes.c_int32), ("m_fp64", ctypes.c_int32),
+                ("split", ctypes.c_int32)]
 
 
 class _LQ(ctypes.Structure):
@@ -207,14 +208,14 @@ class Plan:
     """
 
     def __init__(self, n: int, m: int, N, stage_off, warps: int = 0, refine: bool = False,
-                 inst_per_cta: int = 0, m_fp64: bool = False):
+                 inst_per_cta: int = 0, m_fp64: bool = False, split: bool = False):
         self.n, self.m = int(n), int(m)
         self.N = np.ascontiguousarray(np.asarray(N, dtype=np.int32))
         self.stage_off = np.ascontiguousarray(np.asarray(stage_off, dtype=np.int64))
         self.count = int(self.N.size)
         self.total = int((self.stage_off + self.N + 1).max())
         b = _Batch(self.n, self.m, self.count, self.N.ctypes.data, self.stage_off.ctypes.data)
-        o = _Opts(int(warps), int(bool(refine)), int(inst_per_cta), int(bool(m_fp64)))
+        o = _Opts(int(warps), int(bool(refine)), int(inst_per_cta), int(bool(m_fp64)), int(bool(split)))
         h = _vp()
         _check(_lib.pdilqr_plan_create(ctypes.byref(b), ctypes.byref(o), ctypes.byref(h)),
                "pdilqr_plan_create")

@@ -345,3 +345,55 @@ def test_m_fp64_rejected_elsewhere():
         with pytest.raises(pdilqr.PdilqrError) as e:
             pdilqr.Plan(n, m, [10, 20], [0, 11], m_fp64=True)
         assert e.value.code == pdilqr.E_INVALID_ARG
+
+
+@pytest.mark.parametrize("n,warps,Ns,refine", [(48, 8, [1, 3, 17, 50], False),
+                                               (48, 16, [2, 16, 33, 50], False),
+                                               (96, 16, [5, 50], True), (192, 16, [20], True)])
+def test_split_scan_parity(n, warps, Ns, refine):
+    """The scan with its horizon chunks on separate CTAs (one per chunk,
+    bounded barriers between the phases): uneven horizons, horizons shorter
+    than the chunk count, against the oracle.  At n = 96 and 192 the FP32
+    solve of this recipe alone misses 1e-4 with every solver (the sequential
+    recursion included: M = I + C1 P2 and G are ill-conditioned at these
+    sizes), so there the parity is that of the precision line: one
+    refinement step against the FP64 residual, and the backward error."""
+    from paper_2506_07823_b300.pdilqr import Plan, backward_error
+    insts, packed, Nv, off, s = make_batch(n, n, Ns, seed=7000 + n + warps)
+    plan = Plan(n, n, Nv, off, warps=warps, split=True, refine=refine)
+    assert plan.warps == warps
+    lq, sd = to_dev(packed, s, False)
+    out = plan.kkt_scan_solve(lq, sd, want_policy=not refine, want_resid=refine)
+    torch.cuda.synchronize()
+    check_parity(insts, Nv, off, out, s, False, policy=not refine)
+    if refine:
+        assert float(backward_error(out["resid"]).max()) <= BWD_TOL
+    # the chunks really ran apart: the result differs from the one-chunk
+    # recursion's in its rounding
+    seq = Plan(n, n, Nv, off, warps=1, refine=refine).kkt_scan_solve(lq, sd)
+    torch.cuda.synchronize()
+    assert not torch.equal(out["dx"], seq["dx"])
+
+
+def test_split_scan_refined_twice():
+    """The refinement step's correction solve goes through the split scan too;
+    two solves in a row on one plan (the phase counters restart at zero)."""
+    from paper_2506_07823_b300.pdilqr import Plan, backward_error
+    insts, packed, Nv, off, s = make_batch(96, 96, [40, 7, 25], seed=7096)
+    plan = Plan(96, 96, Nv, off, split=True, refine=True)
+    lq, sd = to_dev(packed, s, False)
+    for _ in range(2):
+        out = plan.kkt_scan_solve(lq, sd, want_resid=True)
+        torch.cuda.synchronize()
+        check_parity(insts, Nv, off, out, s, False)
+        assert float(backward_error(out["resid"]).max()) <= BWD_TOL
+
+
+def test_split_scan_rejected_elsewhere():
+    """Chunks on separate CTAs exist for the 8-warp-unit sizes (n >= 48) with 8
+    or 16 chunks only."""
+    from paper_2506_07823_b300 import pdilqr
+    for n, m, warps in ((12, 12, 16), (36, 24, 8), (48, 48, 4), (96, 96, 1)):
+        with pytest.raises(pdilqr.PdilqrError) as e:
+            pdilqr.Plan(n, m, [10, 20], [0, 11], warps=warps, split=True)
+        assert e.value.code == pdilqr.E_INVALID_ARG
