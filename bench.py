@@ -958,7 +958,7 @@ def run_sweep(args):
 def measure_sweep(torch, pdilqr, dev, stream, reps):
     """The sweep of ``run_sweep`` with ``reps`` graph replays per point."""
 
-    def latency(nrob, N, warps):
+    def latency(nrob, N, warps, split=False):
         prm = synth.srbd_params(nrob)
         md = pdilqr.srbd_model(prm)
         pr = synth.srbd_problem(N, seed=SEED, nrob=nrob)
@@ -966,7 +966,7 @@ def measure_sweep(torch, pdilqr, dev, stream, reps):
         one = build_device_batch(torch, [pr], pk, Nv, off, pr["x0hat"][None], dev)
         w = {k: v.clone() for k, v in one.items()}
         n = 12 * nrob
-        p = pdilqr.Plan(n, n, Nv, off, warps=warps)
+        p = pdilqr.Plan(n, n, Nv, off, warps=warps, split=split)
         inf = {"iters": torch.zeros(1, device=dev, dtype=torch.int32),
                "status": torch.zeros(1, device=dev, dtype=torch.int32),
                "alpha": None, "J": None, "theta": None}
@@ -978,15 +978,23 @@ def measure_sweep(torch, pdilqr, dev, stream, reps):
                     max_iters=1, info=inf)
         step()
         torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            step()
-        for _ in range(5):
-            g.replay()
-        t = event_times(torch, g.replay, reps, stream)
+        if split:
+            # split plans are not captured: direct calls (CUDA events)
+            for _ in range(2):
+                step()
+            t = event_times(torch, step, max(5, min(reps, 20)), stream)
+        else:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step()
+            for _ in range(5):
+                g.replay()
+            t = event_times(torch, g.replay, reps, stream)
         used = p.warps
+        st = int(inf["status"].item())
         p.close()
-        return {"p50_ms": pct(t, 50), "p99_ms": pct(t, 99), "warps": used}
+        return {"p50_ms": pct(t, 50), "p99_ms": pct(t, 99), "warps": used, "status": st,
+                "ctas_per_instance": used if split else 1}
 
     horizon = []
     for N in (25, 50, 100, 150, 200):
@@ -996,8 +1004,12 @@ def measure_sweep(torch, pdilqr, dev, stream, reps):
     robots = []
     for R in (1, 2, 4, 8, 16):
         sc, ri = latency(R, 50, 0), latency(R, 50, 1)
-        robots.append({"robots": R, "n": 12 * R, "scan": sc, "riccati": ri,
-                       "speedup_p50": ri["p50_ms"] / sc["p50_ms"]})
+        row = {"robots": R, "n": 12 * R, "scan": sc, "riccati": ri,
+               "speedup_p50": ri["p50_ms"] / sc["p50_ms"]}
+        if R >= 4:   # the scan's 16 chunks on 16 CTAs (unfused SQP iteration)
+            row["scan_split"] = latency(R, 50, 16, split=True)
+            row["split_speedup_p50"] = ri["p50_ms"] / row["scan_split"]["p50_ms"]
+        robots.append(row)
     return {"sweep": "one SQP iteration, single instance, CUDA-graph replays",
             "horizon_n12": horizon, "robots_N50": robots,
             "work_ratio_scan_to_riccati": "about 50 n^3 vs 13 n^3 flop per stage (n = m)"}

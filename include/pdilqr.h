@@ -104,8 +104,8 @@ typedef struct {
                         /* the CTAs of an instance meet at bounded barriers */
                         /* between the scan's phases (cooperative launch).  */
                         /* Sizes with n >= 48 only; the LQ solves           */
-                        /* (pdilqr_kkt_scan_solve) use it, the fused SQP    */
-                        /* (pdilqr_solve) does not.  Errors: INVALID_ARG for */
+                        /* (pdilqr_kkt_scan_solve) and the SQP (pdilqr_solve,*/
+                        /* then unfused) use it.  Errors: INVALID_ARG for   */
                         /* other sizes or warps; a launch whose warps x     */
                         /* count CTAs cannot all be resident fails (CUDA).  */
 } pdilqr_opts;
@@ -311,7 +311,13 @@ typedef struct {
  * (device, trajectory layout) hold the warm start on entry and the solution
  * on exit.  Needs n = m = 12 nrob with nrob in {1, 2, 4, 8, 16}.  Sizes
  * whose work areas exceed shared memory (nrob >= 8) run them from a global
- * workspace the plan allocates. */
+ * workspace the plan allocates.  A split plan (pdilqr_opts.split, nrob >= 4)
+ * runs each iteration unfused instead, all on the stream: the linearisation
+ * of every stage into the plan's LQ arrays, the scan with its chunks on
+ * separate CTAs, and one kernel per iteration for the merit of the ten step
+ * sizes, the filter decision and the update (the same rules as the fused
+ * kernel); such plans cannot be captured (pdilqr_solve_capture refuses
+ * them). */
 PDILQR_API pdilqr_status pdilqr_solve(pdilqr_plan *plan, const pdilqr_srbd_model *model,
                                       const pdilqr_sqp_opts *opts, const float *x0hat,
                                       float *x, float *u, float *lam, const float *xref,
@@ -326,7 +332,8 @@ PDILQR_API pdilqr_status pdilqr_solve(pdilqr_plan *plan, const pdilqr_srbd_model
  * arrays rewritten), so the caller refills the inputs between replays.
  * Nothing runs on the GPU during the capture.  The capture uses a private
  * stream in relaxed mode; it may not be called while the calling thread
- * captures another stream.  Errors: as pdilqr_solve, CUDA. */
+ * captures another stream.  Errors: as pdilqr_solve, CUDA; INVALID_ARG for a
+ * split plan. */
 PDILQR_API pdilqr_status pdilqr_solve_capture(pdilqr_plan *plan, const pdilqr_srbd_model *model,
                                               const pdilqr_sqp_opts *opts, const float *x0hat,
                                               float *x, float *u, float *lam, const float *xref,

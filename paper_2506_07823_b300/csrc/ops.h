@@ -38,6 +38,9 @@ struct SizeOps {
     // 0 for other sizes
     cudaError_t (*scan_split)(const KktArgs&, int warps, cudaStream_t);
     size_t (*scan_split_gws_floats)(int warps);
+    // merit, filter decision and update of the unfused SQP iteration that
+    // split plans run (SRBD sizes); null for other sizes
+    cudaError_t (*sqp_step)(const SqpStepArgs&, cudaStream_t);
 };
 
 // Warp counts (horizon chunks) a size supports: 1, 4, 8 or 16 within the

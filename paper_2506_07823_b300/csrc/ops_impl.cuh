@@ -319,6 +319,15 @@ static size_t scan_split_gws_floats(int warps)
     }
 }
 
+// The per-instance SQP step (merit, filter, update) of the unfused iteration
+template <int NX, int NU>
+static cudaError_t launch_sqp_step(const SqpStepArgs& a, cudaStream_t st)
+{
+    if (a.count < 1) return cudaSuccess;
+    sqp_step_kernel<NX, NU><<<a.count, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 // The one-chunk (sequential recursion) fused SQP of small SRBD states: the
 // row-per-lane kernel, two instances per warp, WPC warps per CTA.
 template <int NX, int WPC>
@@ -436,6 +445,7 @@ static SizeOps make_ops()
         o.linearize = launch_linearize<NX, NU>;
         o.lin_ws_floats = lin_ws_floats<NX, NU>();
         o.merit = launch_merit<NX, NU>;
+        o.sqp_step = launch_sqp_step<NX, NU>;
     }
     if constexpr (FUSED) {
         o.sqp = launch_sqp<NX, NU>;

@@ -141,6 +141,18 @@ static pdilqr_status plan_init(pdilqr_plan* pl, const pdilqr_batch* b, const pdi
     if (pl->split) {
         PD_CUDA(pl->alloc(&pl->gws, C * pl->ops->scan_split_gws_floats(pl->warps)));
         PD_CUDA(pl->alloc(&pl->sbar, C));
+        if (pl->ops->sqp_step) {   // the unfused SQP iteration's buffers
+            PD_CUDA(pl->alloc(&pl->lqA, T * n * n));
+            PD_CUDA(pl->alloc(&pl->lqB, T * n * m));
+            PD_CUDA(pl->alloc(&pl->lqc, T * n));
+            PD_CUDA(pl->alloc(&pl->lqQ, T * n * n));
+            PD_CUDA(pl->alloc(&pl->lqR, T * m * m));
+            PD_CUDA(pl->alloc(&pl->lqq, T * n));
+            PD_CUDA(pl->alloc(&pl->lqr, T * m));
+            PD_CUDA(pl->alloc(&pl->sq_thmax, C));
+            PD_CUDA(pl->alloc(&pl->sq_done, C));
+            PD_CUDA(pl->alloc(&pl->sq_s, C * n));
+        }
     } else if (const size_t gw = pl->ops->scan_gws_floats(pl->warps)) {
         PD_CUDA(pl->alloc(&pl->gws, C * gw));
     }
@@ -378,6 +390,66 @@ extern "C" pdilqr_status pdilqr_merit_eval(pdilqr_plan* pl, const pdilqr_srbd_mo
     return PDILQR_OK;
 }
 
+// The SQP of a split plan (the scan's chunks on separate CTAs): an unfused
+// iteration per SQP step (Sec. II-B..II-E), all on the stream -- the
+// linearisation of every stage into the plan's LQ arrays, the split scan of
+// the KKT system (dx_0 from the step kernel), and the step kernel (merit of
+// the ten step sizes, filter decision, update, next dx_0).  Instances that
+// have stopped are skipped by the step kernel; their stages are still
+// linearised and solved by later iterations (the launches are uniform).
+static pdilqr_status solve_split(pdilqr_plan* pl, const pdilqr_srbd_model* md,
+                                 const pdilqr_sqp_opts* o, const float* x0hat, float* x, float* u,
+                                 float* lam, const float* xref, const float* uref,
+                                 const uint8_t* contact, pdilqr_sqp_info* info, cudaStream_t st)
+{
+    if (!pl->ops->sqp_step || !pl->lqA || !pl->ops->linearize) return PDILQR_E_INVALID_ARG;
+    LinArgs la;
+    la.md = *md;
+    la.x = x; la.u = u; la.lam = lam; la.xref = xref; la.uref = uref; la.contact = contact;
+    la.A = pl->lqA; la.B = pl->lqB; la.c = pl->lqc; la.Q = pl->lqQ; la.R = pl->lqR; la.S = nullptr;
+    la.q = pl->lqq; la.r = pl->lqr;
+    la.N = pl->dN;
+    la.off = pl->doff;
+    la.stage_inst = pl->dstage_inst;
+    la.total = pl->total;
+    la.work = pl->lin_ws;
+    const pdilqr_lq lq = {pl->lqA, pl->lqB, pl->lqc, pl->lqQ, pl->lqR, nullptr, pl->lqq, pl->lqr};
+    const KktArgs ka = make_args(pl, &lq, pl->sq_s, pl->ddx, pl->ddu, pl->ddl, nullptr, nullptr,
+                                 nullptr, nullptr, pl->st2);
+    SqpStepArgs sa;
+    sa.md = *md;
+    sa.x0hat = x0hat;
+    sa.x = x; sa.u = u; sa.lam = lam; sa.xref = xref; sa.uref = uref; sa.contact = contact;
+    sa.dx = pl->ddx; sa.du = pl->ddu; sa.dlam = pl->ddl;
+    sa.N = pl->dN;
+    sa.off = pl->doff;
+    sa.count = pl->count;
+    sa.max_iters = o->max_iters;
+    sa.tol_step = o->tol_step;
+    sa.tol_theta = o->tol_theta;
+    sa.c_armijo = o->c_armijo;
+    sa.theta_frac = o->theta_frac;
+    sa.alpha_replay = o->alpha_replay;
+    sa.iters = info->iters;
+    sa.status = info->status;
+    sa.alpha = info->alpha;
+    sa.J = info->J;
+    sa.theta = info->theta;
+    sa.kst = pl->st2;
+    sa.thmax = pl->sq_thmax;
+    sa.done = pl->sq_done;
+    sa.s = pl->sq_s;
+    sa.it = -1;
+    PD_CUDA(pl->ops->sqp_step(sa, st));
+    for (int it = 0; it < o->max_iters; ++it) {
+        PD_CUDA(pl->ops->linearize(la, st));
+        PD_CUDA(pl->ops->scan_split(ka, pl->warps, st));
+        sa.it = it;
+        PD_CUDA(pl->ops->sqp_step(sa, st));
+    }
+    return PDILQR_OK;
+}
+
 extern "C" pdilqr_status pdilqr_solve(pdilqr_plan* pl, const pdilqr_srbd_model* md,
                                       const pdilqr_sqp_opts* o, const float* x0hat, float* x,
                                       float* u, float* lam, const float* xref, const float* uref,
@@ -388,6 +460,8 @@ extern "C" pdilqr_status pdilqr_solve(pdilqr_plan* pl, const pdilqr_srbd_model* 
     if (!x0hat || !x || !u || !lam || !xref || !uref || !contact || !info->iters || !info->status)
         return PDILQR_E_INVALID_ARG;
     if (o->max_iters < 1 || o->max_iters > 32) return PDILQR_E_INVALID_ARG;
+    if (pl->split) return solve_split(pl, md, o, x0hat, x, u, lam, xref, uref, contact, info,
+                                      (cudaStream_t)stream);
     if (pl->ops->sqp_smem(pl->warps) > kSmemMax) return PDILQR_E_INVALID_ARG;
     if (pl->ops->scan_gws_floats(pl->warps) && !pl->gws) return PDILQR_E_INVALID_ARG;
     SqpArgs a;
@@ -421,7 +495,7 @@ extern "C" pdilqr_status pdilqr_solve_capture(pdilqr_plan* pl, const pdilqr_srbd
                                               const float* uref, const uint8_t* contact,
                                               pdilqr_sqp_info* info)
 {
-    if (!pl) return PDILQR_E_INVALID_ARG;
+    if (!pl || pl->split) return PDILQR_E_INVALID_ARG;   // split plans: direct solves only
     cudaStream_t s = nullptr;
     PD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);

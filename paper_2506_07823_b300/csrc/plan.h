@@ -13,6 +13,13 @@ struct pdilqr_plan {
     int m64 = 0;         // 1: FP64 elimination of the scan combines' M (n = 36)
     int split = 0;       // 1: the scan's chunks on separate CTAs (kkt_scan_split_kernel)
     unsigned* sbar = nullptr;  // [count] phase counters of the split scan
+    // unfused SQP iteration of split plans (SRBD sizes): linearised stages,
+    // theta_max, stop flags and dx_0 per instance
+    float *lqA = nullptr, *lqB = nullptr, *lqc = nullptr, *lqQ = nullptr, *lqR = nullptr,
+          *lqq = nullptr, *lqr = nullptr;
+    double* sq_thmax = nullptr;
+    int32_t* sq_done = nullptr;
+    float* sq_s = nullptr;
     int64_t total = 0;
     const pdl::SizeOps* ops = nullptr;
     std::vector<void*> allocs;

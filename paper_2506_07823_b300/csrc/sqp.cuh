@@ -242,5 +242,141 @@ __global__ void __launch_bounds__(256) merit_kernel(const __grid_constant__ Meri
                         a.x0hat + (int64_t)inst * NX, N, nrob, mer);
     if (threadIdx.x < 24) a.out[(int64_t)inst * 24 + threadIdx.x] = mer[threadIdx.x];
 }
+// ---------------------------------------- SQP step of the split-scan solve
+// The unfused SQP iteration of plans whose scan runs over several CTAs (one
+// CTA cannot hold the whole iteration): the stages are linearised into the
+// plan's LQ arrays, the split scan solves the KKT system, and this kernel (one
+// CTA per instance) evaluates the merit of the ten step sizes, takes the
+// filter decision of Sec. II-E with the rules of the fused kernel, applies
+// Eq. (linear_rollout) and writes dx_0 of the next KKT solve.  it = -1
+// initialises the per-instance state; an instance that has stopped (status,
+// convergence or the last iteration) is skipped by later iterations.
+struct SqpStepArgs {
+    pdilqr_srbd_model md;
+    const float* x0hat;
+    float *x, *u, *lam;
+    const float *xref, *uref;
+    const uint8_t* contact;
+    const float *dx, *du, *dlam;
+    const int32_t* N;
+    const int64_t* off;
+    int count;
+    int it, max_iters;
+    float tol_step, tol_theta, c_armijo, theta_frac;
+    const float* alpha_replay;     // [count][max_iters] or null
+    int32_t *iters, *status;       // [count]
+    float* alpha;                  // [count][max_iters] or null
+    double *J, *theta;             // [count] or null
+    const int32_t* kst;            // [count] status of this iteration's KKT solve
+    double* thmax;                 // [count] theta_max, fixed at the first iteration
+    int32_t* done;                 // [count] 1: stopped
+    float* s;                      // [count][n] dx_0 = xhat_0 - x_0 of the next solve
+};
+
+template <int NX, int NU>
+__global__ void __launch_bounds__(256) sqp_step_kernel(const __grid_constant__ SqpStepArgs a)
+{
+    __shared__ double mer[32];
+    __shared__ float alpha_sh;
+    __shared__ int conv_sh;
+    const int inst = blockIdx.x;
+    if (inst >= a.count) return;
+    const int N = a.N[inst];
+    const int64_t off = a.off[inst];
+    const int nrob = a.md.nrob;
+    const float* xh = a.x0hat + (int64_t)inst * NX;
+    float* x = a.x + off * NX;
+    float* u = a.u + off * NU;
+    float* lam = a.lam + off * NX;
+    const float* dx = a.dx + off * NX;
+    const float* du = a.du + off * NU;
+    const float* dl = a.dlam + off * NX;
+    const float* xr = a.xref + off * NX;
+    const float* ur = a.uref + off * NU;
+    const uint8_t* ct = a.contact + off * 4 * nrob;
+    if (a.it < 0) {
+        if (threadIdx.x == 0) {
+            a.done[inst] = 0;
+            a.status[inst] = ST_OK;
+            a.iters[inst] = 0;
+            if (a.alpha)
+                for (int t = 0; t < a.max_iters; ++t) a.alpha[(int64_t)inst * a.max_iters + t] = 0.f;
+        }
+        for (int i = threadIdx.x; i < NX; i += blockDim.x) a.s[(int64_t)inst * NX + i] = xh[i] - x[i];
+        return;
+    }
+    if (a.done[inst]) return;   // uniform over the CTA
+    const int it = a.it;
+    int status = a.kst[inst];
+    bool stop = status != ST_OK;
+    if (!stop) {
+        if (threadIdx.x < 32) mer[threadIdx.x] = 0.0;
+        __syncthreads();
+        merit_block<NX, NU>(a.md, x, u, dx, du, xr, ur, ct, xh, N, nrob, mer);
+        if (threadIdx.x == 0) {
+            const double th0 = mer[1], dphi = mer[2];
+            if (it == 0) a.thmax[inst] = (double)a.theta_frac * fmax(1.0, th0);
+            const double thmax = a.thmax[inst];
+            float alpha = 0.f;
+            double th_new = INFINITY;
+            if (a.alpha_replay) {
+                alpha = a.alpha_replay[(int64_t)inst * a.max_iters + it];
+                for (int t = 0; t < 10; ++t)
+                    if (alpha == ldexpf(1.f, -t)) th_new = mer[13 + t];
+            } else {
+                for (int t = 0; t < 10; ++t) {
+                    const double at = ldexp(1.0, -t);
+                    if (filter_ok(th0, dphi, thmax, at, mer[3 + t], mer[13 + t], a.c_armijo)) {
+                        alpha = (float)at;
+                        th_new = mer[13 + t];
+                        break;
+                    }
+                }
+            }
+            // converged at the rounding floor of the FP32 iterate (as the fused kernel)
+            const double floor_th = (double)(N + 1) * sqrt((double)NX) * 0x1p-23 * fmax(1.0, mer[25]);
+            const bool at_floor = alpha == 0.f && th0 <= floor_th && !a.alpha_replay;
+            alpha_sh = at_floor ? -1.f : alpha;
+            conv_sh = (at_floor || (mer[23] < (double)a.tol_step && th_new < (double)a.tol_theta)) ? 1 : 0;
+            if (a.alpha) a.alpha[(int64_t)inst * a.max_iters + it] = alpha;
+            a.iters[inst] = it + 1;
+        }
+        __syncthreads();
+        const float alpha = alpha_sh;
+        if (alpha == 0.f) {
+            status = ST_LINESEARCH;
+            stop = true;
+        } else if (alpha < 0.f) {
+            stop = true;
+        } else {
+            for (int64_t e = threadIdx.x; e < (int64_t)(N + 1) * NX; e += blockDim.x) {
+                x[e] += alpha * dx[e];
+                lam[e] += alpha * dl[e];
+            }
+            for (int64_t e = threadIdx.x; e < (int64_t)N * NU; e += blockDim.x) u[e] += alpha * du[e];
+            __syncthreads();
+            stop = conv_sh != 0;
+        }
+    }
+    if (it + 1 >= a.max_iters) stop = true;
+    if (stop) {
+        if (a.J || a.theta) {
+            // merit at the returned iterate (only the current-point column is read)
+            __syncthreads();
+            if (threadIdx.x < 32) mer[threadIdx.x] = 0.0;
+            __syncthreads();
+            merit_block<NX, NU>(a.md, x, u, dx, du, xr, ur, ct, xh, N, nrob, mer);
+        }
+        if (threadIdx.x == 0) {
+            a.status[inst] = status;
+            a.done[inst] = 1;
+            if (a.J) a.J[inst] = mer[0];
+            if (a.theta) a.theta[inst] = mer[1];
+        }
+    } else {
+        for (int i = threadIdx.x; i < NX; i += blockDim.x) a.s[(int64_t)inst * NX + i] = xh[i] - x[i];
+    }
+}
+
 
 }  // namespace pdl

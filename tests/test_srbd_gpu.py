@@ -436,3 +436,39 @@ def test_autotune_picks_a_timed_configuration():
     solve(pdilqr.Plan(12, 12, Nv, off, warps=plan.warps))
     torch.cuda.synchronize()
     assert rel(got.double().cpu().numpy(), d["x"].double().cpu().numpy()) <= REL_TOL
+
+
+@pytest.mark.parametrize("nrob,Ns,iters", [(4, [50], 2), (4, [13, 37], 3), (8, [50], 2), (16, [50], 2)])
+def test_split_sqp_parity(nrob, Ns, iters):
+    """The SQP of a split plan (the scan's 16 chunks on 16 CTAs; each iteration
+    unfused: linearisation into the plan's LQ arrays, split scan, merit /
+    filter / update kernel), replaying the oracle's step sizes."""
+    from paper_2506_07823_b300 import pdilqr
+    n = 12 * nrob
+    insts = [synth.srbd_problem(N, seed=900 + 10 * nrob + i, nrob=nrob) for i, N in enumerate(Ns)]
+    packed, Nv, off = synth.pack(insts, synth.SRBD_KEYS)
+    x0 = np.stack([p["x0hat"] for p in insts])
+    prm = synth.srbd_params(nrob)
+    refs = [run_oracle(prm, pr, iters) for pr in insts]
+    d = dev(packed)
+    plan = pdilqr.Plan(n, n, Nv, off, warps=16, split=True)
+    replay = torch.tensor(np.stack([r[3]["alpha"] for r in refs]).astype(np.float32), device="cuda")
+    info = plan.solve(pdilqr.srbd_model(prm), torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                      d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"],
+                      max_iters=iters, alpha_replay=replay)
+    torch.cuda.synchronize()
+    assert np.all(info["status"].cpu().numpy() == 0), info["status"]
+    assert np.all(info["iters"].cpu().numpy() == iters), info["iters"]
+    np.testing.assert_array_equal(info["alpha"].cpu().numpy(), replay.cpu().numpy())
+    xs, us, ls = (d[k].double().cpu().numpy() for k in ("x", "u", "lam"))
+    for i, (xr, ur, lr, inf) in enumerate(refs):
+        N, o = int(Nv[i]), int(off[i])
+        sl = slice(o, o + N + 1)
+        assert rel(xs[sl], xr) <= REL_TOL, (i, rel(xs[sl], xr))
+        assert rel(us[o:o + N], ur[:N]) <= REL_TOL, (i, rel(us[o:o + N], ur[:N]))
+        assert rel(ls[sl], lr) <= REL_TOL, (i, rel(ls[sl], lr))
+        assert abs(info["J"][i].item() - inf["J"]) <= 1e-4 * abs(inf["J"])
+    from paper_2506_07823_b300.pdilqr import PdilqrError
+    with pytest.raises(PdilqrError):
+        plan.capture(pdilqr.srbd_model(prm), torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                     d["x"], d["u"], d["lam"], d["xref"], d["uref"], d["contact"], max_iters=iters)
