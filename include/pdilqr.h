@@ -136,9 +136,15 @@ PDILQR_API int32_t pdilqr_plan_warps(const pdilqr_plan *plan);
  *   (pdilqr_riccati_solve) issues none of its bulk stage copies, so the
  *   bounded wait for the first one runs out (about 0.6 s per CTA); the
  *   instance ends with status PDILQR_E_TIMEOUT and the context stays usable.
+ *   PDILQR_DEBUG_SPLIT_SKIP_ARRIVE: in the split scan (pdilqr_opts.split) the
+ *   CTA of chunk 0 does not arrive at the first barrier between the scan's
+ *   phases, so the bounded wait of every CTA of the instance runs out (about
+ *   2 s); the instance ends with PDILQR_E_TIMEOUT (its results are not
+ *   meaningful) and the context stays usable.
  * Errors: INVALID_ARG (unknown bits). */
 #define PDILQR_DEBUG_TC_SKIP_ISSUE 1
 #define PDILQR_DEBUG_BULK_SKIP_ISSUE 2
+#define PDILQR_DEBUG_SPLIT_SKIP_ARRIVE 4
 PDILQR_API pdilqr_status pdilqr_plan_set_debug(pdilqr_plan *plan, int32_t flags);
 
 /* ------------------------------------------------------- LQ KKT solves */

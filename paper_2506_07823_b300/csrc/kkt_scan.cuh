@@ -702,15 +702,20 @@ struct UseTc {
 // before the barrier are published by thread 0's fence before its arrival,
 // and the fence after the wait orders the reads that follow.  The wait is
 // bounded (2 s by the global timer): a barrier that does not complete sets
-// `late` (thread 0's) and lets the CTA go on, so that the kernel always ends.
-__device__ __forceinline__ void split_barrier(unsigned* cnt, unsigned target, int& late)
+// `late` (thread 0's) and lets the CTA go on, so that the kernel always ends;
+// once late, the CTA still arrives at later barriers but waits at none, so
+// that a failed instance costs one timeout, not one per phase.  skip_arrive
+// (a test switch) leaves this CTA's arrival out, so that the others' wait
+// runs out with nothing in flight.
+__device__ __forceinline__ void split_barrier(unsigned* cnt, unsigned target, int& late,
+                                              bool skip_arrive = false)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(cnt, 1u);
+        if (!skip_arrive) atomicAdd(cnt, 1u);
         const uint64_t t0 = globaltimer_ns();
-        while (*(volatile unsigned*)cnt < target) {
+        while (!late && *(volatile unsigned*)cnt < target) {
             if (globaltimer_ns() - t0 > 2000000000ull) {
                 late = 1;
                 break;
@@ -757,8 +762,13 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     int late = 0;             // thread 0: a split barrier that ran out
     unsigned sb_phase = 0;
     auto phase_sync = [&]() {
-        if constexpr (SPLIT) split_barrier(sbar, (++sb_phase) * (unsigned)gridDim.x, late);
-        else __syncthreads();
+        if constexpr (SPLIT) {
+            ++sb_phase;
+            const bool skip = (a.dbg & PDILQR_DEBUG_SPLIT_SKIP_ARRIVE) && warp == 0 && sb_phase == 1;
+            split_barrier(sbar, sb_phase * (unsigned)gridDim.x, late, skip);
+        } else {
+            __syncthreads();
+        }
     };
     const int S = N + 1;
     const int Weff = W < S ? W : S;

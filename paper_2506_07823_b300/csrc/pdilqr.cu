@@ -193,7 +193,8 @@ extern "C" int32_t pdilqr_plan_warps(const pdilqr_plan* pl) { return pl ? pl->wa
 
 extern "C" pdilqr_status pdilqr_plan_set_debug(pdilqr_plan* pl, int32_t flags)
 {
-    if (!pl || (flags & ~(PDILQR_DEBUG_TC_SKIP_ISSUE | PDILQR_DEBUG_BULK_SKIP_ISSUE)))
+    if (!pl || (flags & ~(PDILQR_DEBUG_TC_SKIP_ISSUE | PDILQR_DEBUG_BULK_SKIP_ISSUE |
+                          PDILQR_DEBUG_SPLIT_SKIP_ARRIVE)))
         return PDILQR_E_INVALID_ARG;
     pl->dbg = flags;
     return PDILQR_OK;

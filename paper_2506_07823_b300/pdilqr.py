@@ -116,6 +116,7 @@ _lib.pdilqr_plan_warps.restype = ctypes.c_int32
 _lib.pdilqr_plan_set_debug.argtypes = [_vp, ctypes.c_int32]
 DEBUG_TC_SKIP_ISSUE = 1
 DEBUG_BULK_SKIP_ISSUE = 2
+DEBUG_SPLIT_SKIP_ARRIVE = 4
 for _f in ("pdilqr_kkt_scan_solve", "pdilqr_riccati_solve"):
     getattr(_lib, _f).argtypes = [_vp, ctypes.POINTER(_LQ), _vp, ctypes.POINTER(_KktOut), _vp]
 _lib.pdilqr_kkt_residual.argtypes = [_vp, ctypes.POINTER(_LQ), _vp, _vp, _vp, _vp, _vp, _vp]
@@ -225,7 +226,7 @@ class Plan:
 
     def set_debug(self, flags: int):
         """Test switches of the plan (``DEBUG_TC_SKIP_ISSUE``,
-        ``DEBUG_BULK_SKIP_ISSUE``); 0 clears them."""
+        ``DEBUG_BULK_SKIP_ISSUE``, ``DEBUG_SPLIT_SKIP_ARRIVE``); 0 clears them."""
         _check(_lib.pdilqr_plan_set_debug(self._h, int(flags)), "pdilqr_plan_set_debug")
 
     def close(self):

@@ -397,3 +397,25 @@ def test_split_scan_rejected_elsewhere():
         with pytest.raises(pdilqr.PdilqrError) as e:
             pdilqr.Plan(n, m, [10, 20], [0, 11], warps=warps, split=True)
         assert e.value.code == pdilqr.E_INVALID_ARG
+
+
+def test_split_scan_barrier_timeout_status():
+    """The bounded barrier of the split scan: with the test switch that keeps
+    chunk 0 from arriving at the first barrier (nothing in flight), every CTA's
+    wait runs out, the instance ends with E_TIMEOUT within a few seconds, and
+    the next solve on the same plan is correct."""
+    import time
+    from paper_2506_07823_b300 import pdilqr
+    insts, packed, Nv, off, s = make_batch(48, 48, [30], seed=4848)
+    plan = pdilqr.Plan(48, 48, Nv, off, warps=8, split=True)
+    lq, sd = to_dev(packed, s, False)
+    plan.set_debug(pdilqr.DEBUG_SPLIT_SKIP_ARRIVE)
+    t0 = time.time()
+    out = plan.kkt_scan_solve(lq, sd)
+    torch.cuda.synchronize()
+    assert out["status"].item() == pdilqr.E_TIMEOUT
+    assert time.time() - t0 < 30.0
+    plan.set_debug(0)
+    out = plan.kkt_scan_solve(lq, sd)
+    torch.cuda.synchronize()
+    check_parity(insts, Nv, off, out, s, False)
