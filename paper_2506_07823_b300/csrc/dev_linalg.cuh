@@ -1476,6 +1476,215 @@ __device__ bool spd_solve_smem(const Grp<NT>& g, const float* G, int ldg, float*
     return ok;
 }
 
+// M^-1 X for a general M x M matrix (G, global or shared, read only; rows of
+// stride ldg) and NR right-hand sides X (overwritten by the solution) by a
+// group of NT threads, with the factorisation resident in the group's factor
+// buffer (spd_smem_floats(M) floats, the layout of spd_solve_smem): G is
+// copied in and factored P G = L U by Gauss elimination with partial pivoting
+// (right-looking, unblocked: at step k warp 0 picks the row of largest
+// magnitude in column k, all threads exchange the two rows whole, and every
+// thread then eliminates one row below the pivot against the pivot row, read
+// by broadcast), and X is solved in blocks of SMEM_CB columns staged beside
+// the factor through the row permutation (forward substitution with the unit
+// lower factor, then back substitution with U).  wsc: 3 M words of scratch
+// (pivot rows, the row map, the reciprocal pivots).  Returns false
+// (uniformly) if a pivot's magnitude is below 1e-30 or not finite.
+template <int M, int NR, int NT>
+__device__ bool lu_solve_smem(const Grp<NT>& g, const float* G, int ldg, float* X, int ldx, float* wsc)
+{
+    constexpr int LD = M + 1;   // odd row stride: threads on different rows hit different banks
+    float* L = g.fb;
+    float* Xs = g.fb + round4(M * LD);
+    int* prow = reinterpret_cast<int*>(wsc);        // [M] pivot row of step k
+    int* rmap = prow + M;                           // [M] original row at position i
+    float* piv = wsc + 2 * M;                       // [M] 1 / U_kk
+    const bool gsh = __isShared(G);
+    for (int e = g.t; e < M * M; e += NT) {
+        const int i = e / M, k = e - i * M;
+        if (gsh) L[i * LD + k] = G[(size_t)i * ldg + k];
+        else cp_async4(L + i * LD + k, G + (size_t)i * ldg + k);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    // the right-hand-side area is idle during the factorisation: word 0 holds
+    // the "every pivot usable" flag, word 1 the pivot row of the current step
+    float* okw = Xs;
+    int* pw = reinterpret_cast<int*>(Xs + 1);
+    if (g.t == 0) okw[0] = 1.f;
+    g.sync();
+    for (int k = 0; k < M; ++k) {
+        if (g.t < 32) {
+            float best = -1.f;
+            int bi = k;
+            for (int i = k + g.t; i < M; i += 32) {
+                const float a = fabsf(L[i * LD + k]);
+                if (a > best) { best = a; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (g.t == 0) {
+                pw[0] = bi;
+                prow[k] = bi;
+                if (!(best > 1e-30f) || !isfinite(best)) okw[0] = 0.f;
+            }
+        }
+        g.sync();
+        const int p = pw[0];
+        if (p != k)
+            for (int c = g.t; c < M; c += NT) {
+                const float a = L[k * LD + c];
+                L[k * LD + c] = L[p * LD + c];
+                L[p * LD + c] = a;
+            }
+        g.sync();
+        const float ukk = L[k * LD + k];
+        const float inv = 1.f / ukk;
+        if (g.t == 0) piv[k] = inv;
+        for (int i = k + 1 + g.t; i < M; i += NT) {
+            const float l = L[i * LD + k] * inv;
+            L[i * LD + k] = l;
+            for (int j = k + 1; j < M; ++j) L[i * LD + j] = fmaf(-l, L[k * LD + j], L[i * LD + j]);
+        }
+        g.sync();
+    }
+    const bool ok = okw[0] != 0.f;
+    if (g.t == 0) {
+        for (int i = 0; i < M; ++i) rmap[i] = i;
+        for (int k = 0; k < M; ++k) {
+            const int p = prow[k], t = rmap[k];
+            rmap[k] = rmap[p];
+            rmap[p] = t;
+        }
+    }
+    __threadfence_block();
+    g.sync();   // the flag and the row map are read before the right-hand sides overwrite them
+    static_assert(NT % SMEM_CB == 0, "whole rows of a block per pass");
+    constexpr int RPP = NT / SMEM_CB;
+    const int cc = g.t % SMEM_CB, rr = g.t / SMEM_CB;
+    constexpr int DB = M % 32 == 0 ? 32 : M % 16 == 0 ? 16 : M % 8 == 0 ? 8 : M % 4 == 0 ? 4
+                     : M % 2 == 0 ? 2 : 1;
+    const int tx = g.t % 16, ty = g.t / 16;   // 16 column groups x NT / 16 row offsets
+    constexpr int TY = NT / 16, QR = (M + TY - 1) / TY;
+    for (int c0 = 0; c0 < NR; c0 += SMEM_CB) {
+        const bool on = c0 + cc < NR;
+        const bool xsh = __isShared(X);
+        // staged through the row permutation: position r holds original row rmap[r]
+        for (int r = rr; r < M; r += RPP) {
+            const float* src = X + (size_t)rmap[r] * ldx + c0 + cc;
+            if (!on) Xs[r * SMEM_CB + cc] = 0.f;
+            else if (xsh) Xs[r * SMEM_CB + cc] = *src;
+            else cp_async4(Xs + r * SMEM_CB + cc, src);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        g.sync();
+        // L Y = P X (unit lower factor) by diagonal blocks of DB rows
+        for (int kb = 0; kb < M; kb += DB) {
+            const int ke = kb + DB;
+            if (g.t < SMEM_CB) {
+                float y[DB];
+#pragma unroll
+                for (int i = 0; i < DB; ++i) y[i] = Xs[(kb + i) * SMEM_CB + g.t];
+#pragma unroll
+                for (int i = 0; i < DB; ++i)
+#pragma unroll
+                    for (int r = i + 1; r < DB; ++r) y[r] = fmaf(-L[(kb + r) * LD + kb + i], y[i], y[r]);
+#pragma unroll
+                for (int i = 0; i < DB; ++i) Xs[(kb + i) * SMEM_CB + g.t] = y[i];
+            }
+            g.sync();
+            if (ke < M) {
+                float acc[QR][4];
+#pragma unroll
+                for (int q = 0; q < QR; ++q)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+                for (int k = kb; k < ke; ++k) {
+                    const float4 y = *reinterpret_cast<const float4*>(Xs + k * SMEM_CB + 4 * tx);
+#pragma unroll
+                    for (int q = 0; q < QR; ++q) {
+                        const int r = ke + ty + TY * q;
+                        const float l = r < M ? L[r * LD + k] : 0.f;
+                        acc[q][0] = fmaf(l, y.x, acc[q][0]);
+                        acc[q][1] = fmaf(l, y.y, acc[q][1]);
+                        acc[q][2] = fmaf(l, y.z, acc[q][2]);
+                        acc[q][3] = fmaf(l, y.w, acc[q][3]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < QR; ++q) {
+                    const int r = ke + ty + TY * q;
+                    if (r < M) {
+                        float4* px = reinterpret_cast<float4*>(Xs + r * SMEM_CB + 4 * tx);
+                        float4 v = *px;
+                        v.x -= acc[q][0]; v.y -= acc[q][1]; v.z -= acc[q][2]; v.w -= acc[q][3];
+                        *px = v;
+                    }
+                }
+                g.sync();
+            }
+        }
+        // U Z = Y by the same blocks from the bottom up: rows above a block
+        // lose U[r][block] z[block]
+        for (int kb = M - DB; kb >= 0; kb -= DB) {
+            const int ke = kb + DB;
+            if (g.t < SMEM_CB) {
+                float z[DB];
+#pragma unroll
+                for (int i = 0; i < DB; ++i) z[i] = Xs[(kb + i) * SMEM_CB + g.t];
+#pragma unroll
+                for (int i = DB - 1; i >= 0; --i) {
+                    z[i] *= piv[kb + i];
+#pragma unroll
+                    for (int r = 0; r < i; ++r) z[r] = fmaf(-L[(kb + r) * LD + kb + i], z[i], z[r]);
+                }
+#pragma unroll
+                for (int i = 0; i < DB; ++i) Xs[(kb + i) * SMEM_CB + g.t] = z[i];
+            }
+            g.sync();
+            if (kb > 0) {
+                float acc[QR][4];
+#pragma unroll
+                for (int q = 0; q < QR; ++q)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+                for (int k = kb; k < ke; ++k) {
+                    const float4 z = *reinterpret_cast<const float4*>(Xs + k * SMEM_CB + 4 * tx);
+#pragma unroll
+                    for (int q = 0; q < QR; ++q) {
+                        const int r = ty + TY * q;
+                        const float u = r < kb ? L[r * LD + k] : 0.f;
+                        acc[q][0] = fmaf(u, z.x, acc[q][0]);
+                        acc[q][1] = fmaf(u, z.y, acc[q][1]);
+                        acc[q][2] = fmaf(u, z.z, acc[q][2]);
+                        acc[q][3] = fmaf(u, z.w, acc[q][3]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < QR; ++q) {
+                    const int r = ty + TY * q;
+                    if (r < kb) {
+                        float4* px = reinterpret_cast<float4*>(Xs + r * SMEM_CB + 4 * tx);
+                        float4 v = *px;
+                        v.x -= acc[q][0]; v.y -= acc[q][1]; v.z -= acc[q][2]; v.w -= acc[q][3];
+                        *px = v;
+                    }
+                }
+                g.sync();
+            }
+        }
+        for (int r = rr; r < M; r += RPP)
+            if (on) X[(size_t)r * ldx + c0 + cc] = Xs[r * SMEM_CB + cc];
+        g.sync();
+    }
+    return ok;
+}
+
+
 // ---------------------------------------------------------------- dispatch
 // One-warp groups use the register versions (they need a small shared
 // scratch: `wsc`, at least 2 * (max(M, N) + 3) floats); wider groups use the

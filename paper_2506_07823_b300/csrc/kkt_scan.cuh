@@ -308,6 +308,12 @@ __device__ __forceinline__ bool m_solve(const Grp<NT>& g, float* G, int ld, floa
     if constexpr (NX == 36 && NX + NR <= NT) {
         if (m64) return m_solve_f64<NX, NR, NT>(g, G, ld, reinterpret_cast<double*>(g.tb ? g.tb : dscr));
     }
+    // large states whose unit has a factor buffer (the split scan's CTAs): LU
+    // with partial pivoting of M in shared memory, the right-hand sides solved
+    // in blocks there, instead of the elimination in place in the work area
+    if constexpr (NX >= kSmemFactorRows && NT >= SMEM_CB && NT % SMEM_CB == 0) {
+        if (g.fb && g.fbn >= spd_smem_floats(NX)) return lu_solve_smem<NX, NR, NT>(g, G, ld, G + NX, ld, wsc);
+    }
     return gj_solve<NX, NR, NT>(g, G, ld, wsc);
 }
 
