@@ -53,3 +53,17 @@ def test_plan_rejects_bad_batches_without_gpu_work():
         pdilqr.Plan(4, 2, [4], [0], warps=5)     # unsupported warp count
     with pytest.raises(pdilqr.PdilqrError):
         pdilqr.Plan(4, 2, [4], [0], warps=2)
+
+
+def test_autotune_candidates_cover_the_configurations():
+    """The batch autotuner's candidate list (host logic, no GPU): the one-robot
+    size times the sequential recursion at 2, 4 and 8 instances per CTA and
+    the scan at 4, 8 and 16 chunks; other sizes the solver and chunk count;
+    every label is distinct."""
+    from paper_2506_07823_b300 import autotune
+    c12 = autotune.candidates(12, 12)
+    assert {(1, 2), (1, 4), (1, 8), (4, 0), (8, 0), (16, 0)} == set(c12)
+    assert set(autotune.candidates(48, 48)) == {(1, 0), (4, 0), (8, 0), (16, 0)}
+    labels = [autotune.label(w, i) for w, i in c12]
+    assert len(set(labels)) == len(labels)
+    assert autotune.label(1, 8) == "seq/8" and autotune.label(16, 0) == "scan/16"
