@@ -419,3 +419,17 @@ def test_split_scan_barrier_timeout_status():
     out = plan.kkt_scan_solve(lq, sd)
     torch.cuda.synchronize()
     check_parity(insts, Nv, off, out, s, False)
+
+
+def test_split_scan_with_cross_term_S():
+    """The split scan with a nonzero cross term S (element build through
+    R^-1 [B^T | S | r]) at n = 96, where the combines take the shared-memory LU
+    of M, through the refinement step."""
+    from paper_2506_07823_b300.pdilqr import Plan, backward_error
+    insts, packed, Nv, off, s = make_batch(96, 96, [30, 9], seed=9696, with_S=True)
+    plan = Plan(96, 96, Nv, off, warps=16, split=True, refine=True)
+    lq, sd = to_dev(packed, s, True)
+    out = plan.kkt_scan_solve(lq, sd, want_resid=True)
+    torch.cuda.synchronize()
+    check_parity(insts, Nv, off, out, s, True)
+    assert float(backward_error(out["resid"]).max()) <= BWD_TOL
