@@ -433,3 +433,23 @@ def test_split_scan_with_cross_term_S():
     torch.cuda.synchronize()
     check_parity(insts, Nv, off, out, s, True)
     assert float(backward_error(out["resid"]).max()) <= BWD_TOL
+
+
+def test_split_scan_refuses_a_grid_that_cannot_be_resident():
+    """The split scan's CTAs wait on one another, so all chunks x instances of a
+    launch must be resident together: at n = 192 (one CTA per SM) ten
+    instances of 16 chunks (160 CTAs) are refused on the host before any
+    kernel runs, and the same plan shape with nine instances solves."""
+    from paper_2506_07823_b300 import pdilqr
+    Ns = [4] * 10
+    insts, packed, Nv, off, s = make_batch(192, 192, Ns, seed=19210)
+    lq, sd = to_dev(packed, s, False)
+    plan = pdilqr.Plan(192, 192, Nv, off, warps=16, split=True)
+    with pytest.raises(pdilqr.PdilqrError) as e:
+        plan.kkt_scan_solve(lq, sd)
+        torch.cuda.synchronize()
+    assert e.value.code == pdilqr.E_CUDA
+    plan9 = pdilqr.Plan(192, 192, Nv[:9], off[:9], warps=16, split=True)
+    out = plan9.kkt_scan_solve(lq, sd)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
