@@ -298,8 +298,16 @@ __device__ __forceinline__ void srbd_lin_rows12(const Grp<16>& g, float* st,
     const float* ur = in + 72;
     const uint8_t* ct = reinterpret_cast<const uint8_t*>(in + 84);
     float row[12];
+    // the lane's weights, read with static indices (a lane-dependent index
+    // into the kernel parameters would serialise the lanes' constant-cache
+    // reads) and selected
+    float wq = 0.f, wu = 0.f;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        wq = j == r ? (terminal ? md.WN[j] : md.W[j]) : wq;
+        wu = j == r ? md.Wu[j] : wu;
+    }
     // Q row r and q_r
-    const float wq = terminal ? md.WN[r] : md.W[r];
 #pragma unroll
     for (int j = 0; j < 12; ++j) row[j] = j == r ? wq : 0.f;
     st_row(st + L::Q + r * 12, row);
@@ -366,7 +374,6 @@ __device__ __forceinline__ void srbd_lin_rows12(const Grp<16>& g, float* st,
     st_row(st + L::B + r * 12, row);
     // R row r and r_r: control r is component cp of foot jf
     const int jf = r / 3, cp = r - 3 * jf;
-    const float wu = md.Wu[r];
 #pragma unroll
     for (int j = 0; j < 12; ++j) row[j] = j == r ? wu : 0.f;
     float grad = wu * (u[r] - ur[r]);
