@@ -59,6 +59,33 @@ def flops_per_stage(n: int, solver: str) -> float:
     return (50.0 if solver == "scan" else 13.0) * n ** 3
 
 
+def lq_flops_per_stage(n: int, m: int, solver: str) -> float:
+    """Algorithmic flops of one LQ KKT solve per stage for general (n, m): the
+    sequential recursion 4 n^3 + 8 n^2 m + m^3 / 3; the work-efficient scan
+    the full combine (17 n^3), the value-function combine (8.7 n^3), the
+    element build (m^3 / 3 + 4 m^2 n + 6 n^2 m), the policy (2 n^3 + 4 n^2 m +
+    4 n m^2 + m^3 / 3) and the trajectory (2 n^3 + 2 n^2 m), about 50 n^3 at
+    n = m."""
+    if solver != "scan":
+        return 4.0 * n ** 3 + 8.0 * n * n * m + m ** 3 / 3.0
+    return (17.0 * n ** 3 + 8.7 * n ** 3 + (m ** 3 / 3.0 + 4.0 * m * m * n + 6.0 * n * n * m) +
+            (2.0 * n ** 3 + 4.0 * n * n * m + 4.0 * n * m * m + m ** 3 / 3.0) +
+            (2.0 * n ** 3 + 2.0 * n * n * m))
+
+
+def roofline_rec(flops: float, ms: float, peak_tflops, ctas=None) -> dict:
+    """Achieved algorithmic TFLOP/s of one timed call and its fraction of the
+    measured FP32 FMA peak of the whole GPU (and, for a call that occupies
+    `ctas` SMs of the 148, of those SMs' share of it)."""
+    ach = flops / (ms / 1e3) / 1e12
+    rec = {"algorithmic_flops": flops, "achieved_tflops": ach}
+    if peak_tflops:
+        rec["frac_of_ffma_peak"] = ach / peak_tflops
+        if ctas:
+            rec["frac_of_ffma_peak_of_its_sms"] = ach / (peak_tflops * ctas / 148.0)
+    return rec
+
+
 def _gj_flops(rows: int, cols: int) -> float:
     """Gauss-Jordan elimination of a rows x (rows + cols) augmented matrix as
     the kernels run it: every step updates the rows - 1 other rows over the
@@ -433,7 +460,8 @@ def run_gpu(args):
         except Exception:
             traffic = None
         extras = measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, plans, args)
-        lqw = measure_lq_workloads(torch, pdilqr, dev, stream, args) if args.lq_workloads else None
+        lqw = (measure_lq_workloads(torch, pdilqr, dev, stream, args, peak_ffma)
+               if args.lq_workloads else None)
         serving = None
         if args.serve_seconds > 0:
             low = args.serve_rate_sustained
@@ -683,7 +711,7 @@ def measure_extras(torch, pdilqr, md, prm, dev, stream, base, work, plan, plans,
     return {"latency": lat, "comparators": comp}
 
 
-def measure_large_state_lq(torch, pdilqr, oracle, dev, stream, args):
+def measure_large_state_lq(torch, pdilqr, oracle, dev, stream, args, peak=None):
     """One instance's LQ KKT solve at the centralised multi-robot sizes (n = m =
     12 R for R = 4, 8, 16; N = 50; the whole-body LTV recipe at that size) by
     the sequential recursion (one CTA), the scan over 4 chunks inside one CTA,
@@ -718,6 +746,10 @@ def measure_large_state_lq(torch, pdilqr, oracle, dev, stream, args):
                 err = max(err, float(np.abs(got - want).max() / np.abs(want).max()))
             row[name] = {"p50_ms": pct(t, 50), "p99_ms": pct(t, 99), "ctas": p1.warps if kw.get("split") else 1,
                          "status": int(o1["status"][0].item()), "max_rel_error_vs_oracle": err}
+            if not kw.get("refine"):
+                solver = "riccati" if kw["warps"] == 1 else "scan"
+                row[name]["roofline"] = roofline_rec(51 * lq_flops_per_stage(n, n, solver), pct(t, 50),
+                                                     peak, row[name]["ctas"])
             p1.close()
         row["split_speedup_vs_sequential"] = row["sequential"]["p50_ms"] / row["scan_split"]["p50_ms"]
         row["split_speedup_vs_sequential_refined"] = (row["sequential_refined"]["p50_ms"] /
@@ -726,7 +758,7 @@ def measure_large_state_lq(torch, pdilqr, oracle, dev, stream, args):
     return rows
 
 
-def measure_lq_workloads(torch, pdilqr, dev, stream, args):
+def measure_lq_workloads(torch, pdilqr, dev, stream, args, peak=None):
     """LQ KKT solves alone: the whole-body-sized batch (n = 36, m = 24,
     N = 100, 1024 instances; 128 distinct instances replicated eight times)
     with the FP64-residual refinement step, scan vs sequential Riccati, the
@@ -771,6 +803,16 @@ def measure_lq_workloads(torch, pdilqr, dev, stream, args):
                "max_rel_error_vs_oracle": max(errs),
                "median_rel_error_vs_oracle": float(np.median(errs)),
                "within_1e-4": int(sum(e <= 1e-4 for e in errs))}
+        if not refine:
+            # the solve kernel alone (no residual): its algorithmic rate
+            o2 = plan.alloc_out(device=dev)
+            fn(lq, sd, out=o2)
+            torch.cuda.synchronize()
+            tk = event_times(torch, lambda: fn(lq, sd, out=o2), 3, stream)
+            solver = "riccati" if warps == 1 else "scan"
+            flops = float(np.sum(Nv + 1)) * lq_flops_per_stage(36, 24, solver)
+            rec["roofline"] = dict(roofline_rec(flops, float(np.mean(tk)), peak),
+                                   solve_ms=float(np.mean(tk)))
         plan.close()
         return rec
 
@@ -810,7 +852,7 @@ def measure_lq_workloads(torch, pdilqr, dev, stream, args):
         t = event_times(torch, g.replay, args.latency_reps, stream)
         single[name] = {"p50_us": pct(t, 50) * 1e3, "p99_us": pct(t, 99) * 1e3}
     out["single_lqr_n4_N16"] = single
-    out["large_state_lq"] = measure_large_state_lq(torch, pdilqr, oracle, dev, stream, args)
+    out["large_state_lq"] = measure_large_state_lq(torch, pdilqr, oracle, dev, stream, args, peak)
     return out
 
 
@@ -1185,8 +1227,9 @@ def main():
         import torch
         from paper_2506_07823_b300 import pdilqr
         torch.cuda.set_device(0)
+        peak, _ = pdilqr.peak_probe(pdilqr.PEAK_FFMA, 3)
         print(json.dumps(measure_lq_workloads(torch, pdilqr, torch.device("cuda", 0),
-                                              torch.cuda.current_stream(), args)), flush=True)
+                                              torch.cuda.current_stream(), args, peak)), flush=True)
         return
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:
