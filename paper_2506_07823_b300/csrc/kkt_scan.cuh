@@ -308,10 +308,11 @@ __device__ __forceinline__ bool m_solve(const Grp<NT>& g, float* G, int ld, floa
     if constexpr (NX == 36 && NX + NR <= NT) {
         if (m64) return m_solve_f64<NX, NR, NT>(g, G, ld, reinterpret_cast<double*>(g.tb ? g.tb : dscr));
     }
-    // large states whose unit has a factor buffer (the split scan's CTAs): LU
-    // with partial pivoting of M in shared memory, the right-hand sides solved
-    // in blocks there, instead of the elimination in place in the work area
-    if constexpr (NX >= kSmemFactorRows && NT >= SMEM_CB && NT % SMEM_CB == 0) {
+    // units with a factor buffer large enough for M (the split scan's CTAs at
+    // n >= 96, the whole-body size's units): LU with partial pivoting of M in
+    // shared memory, the right-hand sides solved in blocks there, instead of
+    // the elimination in place in the work area
+    if constexpr ((NX >= kSmemFactorRows || NX == 36) && NT >= SMEM_CB && NT % SMEM_CB == 0) {
         if (g.fb && g.fbn >= spd_smem_floats(NX)) return lu_solve_smem<NX, NR, NT>(g, G, ld, G + NX, ld, wsc);
     }
     return gj_solve<NX, NR, NT>(g, G, ld, wsc);
@@ -673,12 +674,17 @@ struct UnitTiles {
 
 // Factor buffers of the wide units (shared-memory SPD solves), placed after
 // the tile buffers for kernels whose work areas live in global memory, when
-// they fit.  Only for systems of 96 rows or more: smaller augmented
-// matrices stay in L1 through the elimination in place, and the buffer would
-// take that L1 away from the products.
-template <int NU, int W, int UW>
+// they fit.  For systems of 96 rows or more (smaller augmented matrices stay
+// in L1 through the elimination in place, and the buffer would take that L1
+// away from the products), and for the whole-body size (n, m) = (36, 24),
+// whose 4-warp units spent their time in the barriers and global-memory
+// reads of the in-place eliminations.  The buffer holds max(NX, NU) rows:
+// the SPD systems have NU, the combines' M has NX.
+template <int NU, int W, int UW, int NX = NU>
 struct UnitFactor {
-    static constexpr int FLOATS = (UW > 1 && NU >= kSmemFactorRows) ? spd_smem_floats(NU) : 0;
+    static constexpr int ROWS = NX > NU ? NX : NU;
+    static constexpr bool ON = UW > 1 && (NU >= kSmemFactorRows || (NX == 36 && NU == 24));
+    static constexpr int FLOATS = ON ? spd_smem_floats(ROWS) : 0;
     static constexpr size_t BYTES = (size_t)W * FLOATS * sizeof(float);
     __host__ __device__ static constexpr size_t at(size_t base) { return (base + 15) & ~(size_t)15; }
     __host__ __device__ static constexpr bool fit(size_t base)
@@ -756,7 +762,7 @@ __device__ int scan_solve(const Src& src, const KktArgs& a, int N, int64_t off,
     constexpr int WU = SPLIT ? 1 : W;      // units per CTA
     const int warp = SPLIT ? (int)blockIdx.x : (int)(threadIdx.x / NT);   // the chunk
     const int unit = SPLIT ? 0 : warp;     // the unit within this CTA
-    using UF = UnitFactor<NU, WU, UW>;
+    using UF = UnitFactor<NU, WU, UW, NX>;
     // factor buffers exist for this configuration (the caller passes them
     // whenever they fit); the shared-memory solves are compiled only then
     constexpr bool FAC = UF::FLOATS > 0 && UF::BYTES + UnitTiles<WU, UW>::BYTES + 1024 <= kSmemCta;
@@ -982,7 +988,7 @@ __global__ void __launch_bounds__(W * 32 * UW, MinBlocks<W * UW>::value)
     if (inst >= a.count) return;
     const LqSource src(a);
     float* work = a.gws ? a.gws + (int64_t)blockIdx.x * ScanSmem<NX, NU, W>::TOTAL : smem;
-    using UF = UnitFactor<NU, W, UW>;
+    using UF = UnitFactor<NU, W, UW, NX>;
     const size_t base = a.gws ? 0 : ScanSmem<NX, NU, W>::BYTES;
     float* tiles = TL::fit(base) ? smem + TL::at(base) / sizeof(float) : nullptr;
     const size_t fbase = TL::total(base);

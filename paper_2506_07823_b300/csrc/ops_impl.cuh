@@ -50,7 +50,7 @@ static cudaError_t launch_scan_w(const KktArgs& a, cudaStream_t st)
         // workspace; the wide units' tile buffers after them when they fit
         constexpr bool GWS = SM::BYTES > kSmemMax;
         constexpr size_t tb = UnitTiles<W, UW>::total(GWS ? 0 : SM::BYTES);
-        constexpr size_t bytes = GWS ? UnitFactor<NU, W, UW>::total(tb) : tb;
+        constexpr size_t bytes = GWS ? UnitFactor<NU, W, UW, NX>::total(tb) : tb;
         if (GWS && !a.gws) return cudaErrorInvalidConfiguration;
         static std::atomic<uint64_t> smem_done{0};
         if (cudaError_t e = ensure_smem(kkt_scan_kernel<NX, NU, W, UW>, bytes, smem_done); e != cudaSuccess)
