@@ -395,6 +395,14 @@ typedef struct {
                                /* only while the budget has room and is cut to   */
                                /* it, so that the SMs it leaves serve the small  */
                                /* classes.  0: no budget (streams limit alone)   */
+    int32_t split_min_robots;  /* classes of at least this many robots (4, 8 or   */
+                               /* 16) run split plans: the scan's 16 horizon     */
+                               /* chunks of an instance on 16 CTAs, an unfused   */
+                               /* SQP iteration (as pdilqr_opts.split); at most  */
+                               /* one split batch is in flight.  0: none (every  */
+                               /* class runs the fused kernel)                   */
+    int32_t split_max_batch;   /* most instances of one split batch (0: 4; each   */
+                               /* holds 16 SMs while it runs)                    */
 } pdilqr_serve_opts;
 
 typedef struct {

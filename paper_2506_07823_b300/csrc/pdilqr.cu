@@ -652,6 +652,38 @@ pdilqr_status pdl::plan_create_capacity(int n, int m, int max_count, int64_t slo
     return PDILQR_OK;
 }
 
+pdilqr_status pdl::plan_enable_split(pdilqr_plan* pl, int warps)
+{
+    if (!pl || pl->split || pl->warps != 1 || (warps != 8 && warps != 16)) return PDILQR_E_INVALID_ARG;
+    const SizeOps* ops = pl->ops;
+    if (!ops->scan_split || !ops->sqp_step || !ops->linearize) return PDILQR_E_INVALID_ARG;
+    const size_t n = pl->n, m = pl->m, T = pl->total, C = pl->max_count;
+    PD_CUDA(pl->alloc(&pl->gws, C * ops->scan_split_gws_floats(warps)));
+    PD_CUDA(pl->alloc(&pl->sbar, C));
+    PD_CUDA(pl->alloc(&pl->lqA, T * n * n));
+    PD_CUDA(pl->alloc(&pl->lqB, T * n * m));
+    PD_CUDA(pl->alloc(&pl->lqc, T * n));
+    PD_CUDA(pl->alloc(&pl->lqQ, T * n * n));
+    PD_CUDA(pl->alloc(&pl->lqR, T * m * m));
+    PD_CUDA(pl->alloc(&pl->lqq, T * n));
+    PD_CUDA(pl->alloc(&pl->lqr, T * m));
+    PD_CUDA(pl->alloc(&pl->sq_thmax, C));
+    PD_CUDA(pl->alloc(&pl->sq_done, C));
+    PD_CUDA(pl->alloc(&pl->sq_s, C * n));
+    if (ops->lin_ws_floats && !pl->lin_ws) PD_CUDA(pl->alloc(&pl->lin_ws, ops->lin_ws_floats));
+    pl->warps = warps;
+    pl->split = 1;
+    return PDILQR_OK;
+}
+
+pdilqr_status pdl::plan_set_stage_inst_async(pdilqr_plan* pl, const int64_t* hstage, cudaStream_t st)
+{
+    if (!pl || !hstage) return PDILQR_E_INVALID_ARG;
+    PD_CUDA(cudaMemcpyAsync(pl->dstage_inst, hstage, sizeof(int64_t) * pl->total,
+                            cudaMemcpyHostToDevice, st));
+    return PDILQR_OK;
+}
+
 pdilqr_status pdl::plan_set_batch_async(pdilqr_plan* pl, const int32_t* hN, const int64_t* hoff,
                                         const int32_t* horder, int count, int maxN, cudaStream_t st)
 {

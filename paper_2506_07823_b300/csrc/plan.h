@@ -67,5 +67,14 @@ pdilqr_status plan_create_capacity(int n, int m, int max_count, int64_t slots, i
 // copies): horizons, first slots and CTA order.  Stream-ordered.
 pdilqr_status plan_set_batch_async(pdilqr_plan* pl, const int32_t* hN, const int64_t* hoff,
                                    const int32_t* horder, int count, int maxN, cudaStream_t st);
+// Turn a capacity plan created with one warp into a split plan (the scan's
+// `warps` horizon chunks of an instance on separate CTAs, an unfused SQP
+// iteration): allocates the split scan's work areas and the linearised LQ
+// arrays.  Sizes without a split scan or an SRBD step kernel: INVALID_ARG.
+pdilqr_status plan_enable_split(pdilqr_plan* pl, int warps);
+// Copy the stage-slot -> instance map of the batch (all `slots` entries of
+// the capacity, -1 for a slot of no instance) from pinned host memory; the
+// split plan's linearisation reads it.  Stream-ordered.
+pdilqr_status plan_set_stage_inst_async(pdilqr_plan* pl, const int64_t* hstage, cudaStream_t st);
 
 }  // namespace pdl

@@ -146,6 +146,8 @@ struct ClassRes {  // device and pinned buffers of one size class on one stream
     Entry* htab;
     int32_t *hN, *horder, *hit, *hst;
     int64_t* hoff;
+    int64_t* hstage = nullptr;   // stage slot -> instance (split classes)
+    int64_t slots = 0;           // stage slots of the capacity plan
     float *hx0, *hxr, *hur, *hxo, *huo;
     uint8_t* hct;
     std::vector<void*> dev, host;
@@ -291,6 +293,23 @@ int class_batch(const pdilqr_server* sv, int cls)
 // one- and two-robot classes.
 constexpr int kLargeClass = 2;
 
+// Horizon chunks (CTAs) per instance of a split class.
+constexpr int kSplitChunks = 16;
+
+// Whether size class cls runs a split plan (the server's split_min_robots).
+bool class_split(const pdilqr_server* sv, int cls)
+{
+    return sv->opts.split_min_robots > 0 && (1 << cls) >= sv->opts.split_min_robots;
+}
+
+// Largest batch of size class cls as launched: a split class is also capped
+// by split_max_batch (each instance holds kSplitChunks SMs while it runs).
+int class_cap(const pdilqr_server* sv, int cls)
+{
+    const int b = class_batch(sv, cls);
+    return class_split(sv, cls) ? std::min(b, sv->opts.split_max_batch) : b;
+}
+
 // Device bytes of one stream's batch workspace for size class cls: the
 // capacity plan (policy, value function and closed-loop maps per stage slot,
 // the step buffers, the linearised-stage cache of the scan) and the staging
@@ -298,12 +317,17 @@ constexpr int kLargeClass = 2;
 size_t class_res_bytes(const pdilqr_server* sv, int cls)
 {
     const int nrob = 1 << cls;
-    const size_t n = 12 * (size_t)nrob, B = class_batch(sv, cls);
+    const size_t n = 12 * (size_t)nrob, B = class_cap(sv, cls);
     const size_t S = B * ((size_t)sv->opts.max_N + 1);
     const SizeOps* ops = find_ops((int)n, (int)n);
-    const size_t lq = ops ? (size_t)ops->lq_stage_floats : 0;
+    const bool split = class_split(sv, cls);
+    // a split plan keeps the linearised LQ arrays (A, B, Q, R, c, q, r) and the
+    // stage map instead of the stage cache, and a chunk work area per CTA
+    const size_t lq = split ? 4 * n * n + 5 * n : (ops ? (size_t)ops->lq_stage_floats : 0);
     const size_t per_slot = 3 * n * n + 6 * n + lq + 8 * n + 4 * nrob;
-    return sizeof(float) * S * per_slot + sizeof(float) * B * (n + 16);
+    const size_t gws = (split && ops && ops->scan_split_gws_floats)
+                           ? ops->scan_split_gws_floats(kSplitChunks) : 0;
+    return sizeof(float) * S * per_slot + sizeof(float) * B * (n + 16 + gws);
 }
 
 pdilqr_status ensure_res(pdilqr_server* sv, Slot& sl, int cls)
@@ -311,9 +335,10 @@ pdilqr_status ensure_res(pdilqr_server* sv, Slot& sl, int cls)
     ClassRes& r = sl.res[cls];
     if (r.ready) return PDILQR_OK;
     const int nrob = 1 << cls, n = 12 * nrob, nc = 4 * nrob;
-    const size_t B = class_batch(sv, cls), S = B * ((size_t)sv->opts.max_N + 1);
+    const size_t B = class_cap(sv, cls), S = B * ((size_t)sv->opts.max_N + 1);
     r.n = n;
     r.nc = nc;
+    r.slots = (int64_t)S;
     // the largest warp count not above the requested one whose fused kernel
     // fits in shared memory, else one chunk (the sequential sweep, from the
     // global workspace): a chunk of a large state already fills its SM, so
@@ -321,11 +346,18 @@ pdilqr_status ensure_res(pdilqr_server* sv, Slot& sl, int cls)
     const SizeOps* ops = find_ops(n, n);
     if (!ops || !ops->sqp) return PDILQR_E_INVALID_ARG;
     auto smaller = [](int x) { return x == 16 ? 8 : (x == 8 ? 4 : 1); };
-    int w = sv->opts.warps;
+    const bool split = class_split(sv, cls);
+    int w = split ? 1 : sv->opts.warps;
     while (w > 1 && (!warps_ok(ops, w) || ops->sqp_smem(w) > kSmemMax || ops->scan_gws_floats(w)))
         w = smaller(w);
     pdilqr_status ps = plan_create_capacity(n, n, (int)B, (int64_t)S, w, &r.plan);
     if (ps != PDILQR_OK) return ps;
+    if (split) ps = plan_enable_split(r.plan, kSplitChunks);
+    if (ps != PDILQR_OK) {
+        pdilqr_plan_destroy(r.plan);
+        r.plan = nullptr;
+        return ps;
+    }
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
     chk(dalloc(r, &r.px, S * n)); chk(dalloc(r, &r.pu, S * n)); chk(dalloc(r, &r.pl, S * n));
@@ -337,6 +369,7 @@ pdilqr_status ensure_res(pdilqr_server* sv, Slot& sl, int cls)
     chk(halloc(r, &r.hit, B)); chk(halloc(r, &r.hst, B)); chk(halloc(r, &r.hoff, B));
     chk(halloc(r, &r.hx0, B * n)); chk(halloc(r, &r.hxr, S * n)); chk(halloc(r, &r.hur, S * n));
     chk(halloc(r, &r.hct, S * nc)); chk(halloc(r, &r.hxo, S * n)); chk(halloc(r, &r.huo, S * n));
+    if (split) chk(halloc(r, &r.hstage, S));
     if (e != cudaSuccess) {
         free_res(r);
         return e == cudaErrorMemoryAllocation ? PDILQR_E_NO_MEMORY : PDILQR_E_CUDA;
@@ -417,6 +450,13 @@ pdilqr_status launch_batch(pdilqr_server* sv, Slot& sl, std::vector<Request>& re
     if (cudaGetLastError() != cudaSuccess) return PDILQR_E_CUDA;
     ps = plan_set_batch_async(r.plan, r.hN, r.hoff, r.horder, count, maxN, st);
     if (ps != PDILQR_OK) return ps;
+    if (r.hstage) {   // split plan: its linearisation walks the stage map
+        for (int64_t k = 0; k < r.slots; ++k) r.hstage[k] = -1;
+        for (int i = 0; i < count; ++i)
+            for (int k = 0; k <= r.hN[i]; ++k) r.hstage[r.hoff[i] + k] = i;
+        ps = plan_set_stage_inst_async(r.plan, r.hstage, st);
+        if (ps != PDILQR_OK) return ps;
+    }
     pdilqr_srbd_model md = sv->models[cls];
     md.nrob = 1 << cls;
     pdilqr_sqp_opts so{};
@@ -499,11 +539,14 @@ void worker_loop(pdilqr_server* sv)
         // the oldest request whose client is idle fixes the size class (a large
         // class only while it leaves a stream for the small ones)
         int large_busy = 0, large_ctas = 0;
-        for (const Slot& sl : sv->slots)
+        bool split_busy = false;
+        for (const Slot& sl : sv->slots) {
             if (sl.busy && sl.cls >= kLargeClass) {
                 large_busy += 1;
                 large_ctas += sl.count;
             }
+            if (sl.busy && class_split(sv, sl.cls)) split_busy = true;
+        }
         const int budget = sv->opts.large_cta_budget;
         const bool large_ok = (sv->opts.max_inflight < 2 || large_busy < sv->opts.max_inflight - 1) &&
                               (budget <= 0 || large_ctas < budget);
@@ -513,6 +556,9 @@ void worker_loop(pdilqr_server* sv)
             if (c == sv->clients.end() || c->second.busy) continue;
             const int qc = class_of(q.nrob);
             if (qc >= kLargeClass && !large_ok) continue;
+            // one split batch at a time: its cooperative launch needs all of
+            // its CTAs resident at once
+            if (qc >= 0 && class_split(sv, qc) && split_busy) continue;
             cls = qc;
             break;
         }
@@ -522,7 +568,7 @@ void worker_loop(pdilqr_server* sv)
             }
             std::vector<Request> reqs;
             std::vector<Client*> cl;
-            int cap = class_batch(sv, cls);
+            int cap = class_cap(sv, cls);
             if (cls >= kLargeClass && budget > 0) cap = std::min(cap, budget - large_ctas);
             for (auto it = sv->pending.begin();
                  it != sv->pending.end() && (int)reqs.size() < cap;) {
@@ -594,6 +640,12 @@ extern "C" pdilqr_status pdilqr_serve_create(const pdilqr_serve_opts* o, pdilqr_
     if (sv->opts.max_N <= 0) sv->opts.max_N = 100;
     if (sv->opts.sqp_iters <= 0) sv->opts.sqp_iters = 1;
     if (sv->opts.warps == 0) sv->opts.warps = 8;
+    if (sv->opts.split_max_batch <= 0) sv->opts.split_max_batch = 4;
+    const int smr = sv->opts.split_min_robots;
+    if (smr != 0 && smr != 4 && smr != 8 && smr != 16) {
+        delete sv;
+        return PDILQR_E_INVALID_ARG;
+    }
     if (sv->opts.max_inflight > 16 || sv->opts.large_cta_budget < 0 || sv->opts.max_N > 4096 ||
         sv->opts.sqp_iters > 32 ||
         (sv->opts.warps != 1 && sv->opts.warps != 4 && sv->opts.warps != 8 && sv->opts.warps != 16)) {

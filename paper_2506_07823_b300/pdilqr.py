@@ -369,7 +369,8 @@ class _ServeOpts(ctypes.Structure):
                 ("sqp_iters", ctypes.c_int32), ("warps", ctypes.c_int32),
                 ("batch_window_us", ctypes.c_int32), ("model", SrbdModel),
                 ("class_models", ctypes.POINTER(SrbdModel)), ("hbm_reserve_bytes", ctypes.c_int64),
-                ("large_cta_budget", ctypes.c_int32)]
+                ("large_cta_budget", ctypes.c_int32), ("split_min_robots", ctypes.c_int32),
+                ("split_max_batch", ctypes.c_int32)]
 
 SERVE_NROB = (1, 2, 4, 8, 16)   # the server's size classes (robots per client)
 
@@ -416,12 +417,16 @@ class Server:
     def __init__(self, model_params: dict, hbm_budget_bytes: int = 1 << 30, max_batch: int = 1024,
                  max_inflight: int = 2, max_N: int = 100, sqp_iters: int = 1, warps: int = 8,
                  batch_window_us: int = 0, class_params: dict | None = None,
-                 hbm_reserve_bytes: int = 0, large_cta_budget: int = 0):
+                 hbm_reserve_bytes: int = 0, large_cta_budget: int = 0,
+                 split_min_robots: int = 0, split_max_batch: int = 0):
         """``class_params`` optionally maps a robot count (1, 2, 4, 8, 16) to the
         model constants of that class (formation offsets differ per count);
         classes it does not name use ``model_params``.  ``hbm_reserve_bytes``:
         device memory the free-memory admission check keeps free (0: 256 MiB).
-        ``large_cta_budget``: most instances of 4+ robots in flight (0: none)."""
+        ``large_cta_budget``: most instances of 4+ robots in flight (0: none).
+        ``split_min_robots``: classes of at least this many robots (4, 8, 16) run
+        the split scan, 16 CTAs per instance, one such batch in flight (0: none);
+        ``split_max_batch``: most instances of one split batch (0: 4)."""
         cm = None
         if class_params is not None:
             cm = (SrbdModel * len(SERVE_NROB))(
@@ -429,7 +434,8 @@ class Server:
         o = _ServeOpts(int(hbm_budget_bytes), int(max_batch), int(max_inflight), int(max_N),
                        int(sqp_iters), int(warps), int(batch_window_us), srbd_model(model_params),
                        ctypes.cast(cm, ctypes.POINTER(SrbdModel)) if cm is not None else None,
-                       int(hbm_reserve_bytes), int(large_cta_budget))
+                       int(hbm_reserve_bytes), int(large_cta_budget), int(split_min_robots),
+                       int(split_max_batch))
         h = _vp()
         _check(_lib.pdilqr_serve_create(ctypes.byref(o), ctypes.byref(h)), "pdilqr_serve_create")
         self._h = h

@@ -262,3 +262,39 @@ def test_large_cta_budget_splits_batches():
     with pytest.raises(pdilqr.PdilqrError) as e:
         make_server(large_cta_budget=-1)
     assert e.value.code == pdilqr.E_INVALID_ARG
+
+
+def test_split_classes_match_oracle():
+    """With split_min_robots=4 the four- and eight-robot classes run the split
+    scan (16 CTAs per instance, one split batch in flight, at most two
+    instances per split batch): five four-robot requests of ragged horizons
+    and two eight-robot requests that arrive together, next to one-robot
+    clients, each result the oracle's one real-time iteration; a robot count
+    that is no size class is an invalid split_min_robots."""
+    from paper_2506_07823_b300 import pdilqr
+    cls = {r: synth.srbd_params(r) for r in (1, 4, 8)}
+    srv = make_server(cls[1], class_params=cls, max_N=40, max_inflight=4, split_min_robots=4,
+                      split_max_batch=2, hbm_budget_bytes=256 << 20)
+    r32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    cases = {70: (4, 13), 71: (4, 40), 72: (4, 22), 73: (4, 31), 74: (4, 17), 75: (8, 20),
+             76: (8, 35), 77: (1, 30), 78: (1, 9)}
+    probs = {c: synth.srbd_problem(N, seed=4000 + c, nrob=r) for c, (r, N) in cases.items()}
+    tickets = {c: srv.submit(c, r, N, probs[c]["x0hat"].astype(np.float32), probs[c]["xref"],
+                             probs[c]["uref"], probs[c]["contact"]) for c, (r, N) in cases.items()}
+    for c, (r, N) in cases.items():
+        res = srv.poll(tickets[c], n=12 * r, N=N, timeout_us=60_000_000)
+        assert res["status"] in (0, 8), (c, res["status"])
+        pr = probs[c]
+        x, u, lam, info = oracle.srbd_sqp(cls[r], r32(pr["x0hat"]),
+                                          np.tile(r32(pr["x0hat"]), (N + 1, 1)), r32(pr["uref"]),
+                                          np.zeros((N + 1, 12 * r)), r32(pr["xref"]), r32(pr["uref"]),
+                                          pr["contact"], max_iters=1)
+        assert rel(res["x"], x) <= REL_TOL, (c, rel(res["x"], x))
+        assert rel(res["u"][:-1], u[:-1]) <= REL_TOL, (c, rel(res["u"][:-1], u[:-1]))
+    st = srv.stats()
+    # five four-robot requests in batches of at most two, two eight-robot ones
+    assert st["completed"] == len(cases) and st["batches"] >= 5, st
+    srv.close()
+    with pytest.raises(pdilqr.PdilqrError) as e:
+        make_server(split_min_robots=3)
+    assert e.value.code == pdilqr.E_INVALID_ARG
