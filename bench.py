@@ -232,7 +232,12 @@ def sample_size(cores: int) -> int:
 
 # ------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clock samples (every 200 ms) during the timed region."""
+    """nvidia-smi clock samples (every 200 ms) during the timed region.
+
+    ``start`` returns once nvidia-smi has printed its first sample (at most
+    5 s), so that its start-up does not eat into the region; the summary keeps
+    the last sample taken before the region (the GPU busy with the warm-up
+    steps) and every sample taken inside it."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -243,6 +248,7 @@ class ClockSampler:
         self.proc = None
         self.lines: list[str] = []
         self._t = None
+        self._skip = 0
 
     def start(self):
         try:
@@ -252,6 +258,10 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
+            self._skip = max(0, len(self.lines) - 1)
         except FileNotFoundError:
             self.proc = None
 
@@ -271,7 +281,7 @@ class ClockSampler:
             self._t.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self._skip:]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -486,6 +496,15 @@ def run_gpu(args):
                                                                 args.serve_rate, 1024, 8,
                                                                 args.mix_streams, mix="full",
                                                                 large_cta_budget=args.mix_large_ctas)}
+            if args.mix_split_seconds > 0:
+                serving["full_mix_split_note"] = (
+                    f"the same mix with the classes of {args.mix_split_robots}+ robots on the "
+                    f"split scan (16 CTAs per instance, one split batch in flight, at most "
+                    f"{args.mix_split_batch} instances per split batch)")
+                serving["continuous_batching_full_mix_split"] = measure_serving(
+                    pdilqr, args, args.mix_split_seconds, args.serve_rate, 1024, 8,
+                    args.mix_streams, mix="full", large_cta_budget=args.mix_large_ctas,
+                    split_min_robots=args.mix_split_robots, split_max_batch=args.mix_split_batch)
         e2e = measure_e2e(torch, pdilqr, md, dev, stream, base, plan, args)
         sweep = measure_sweep(torch, pdilqr, dev, stream, args.sweep_reps) if args.sweep_reps > 0 else None
         cpu = None
@@ -958,7 +977,8 @@ def client_robots(c: int, mix: str) -> int:
 
 
 def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, warps: int,
-                    inflight: int, seed: int = 0, mix: str = "pair", large_cta_budget: int = 0):
+                    inflight: int, seed: int = 0, mix: str = "pair", large_cta_budget: int = 0,
+                    split_min_robots: int = 0, split_max_batch: int = 0):
     """Poisson arrivals at ``rate`` requests/s for ``seconds``: each request is
     one real-time SQP iteration of a client's MPC problem (N = 50; robots per
     client as ``client_robots``, several robots coupled by the formation
@@ -970,7 +990,8 @@ def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, w
     srv = pdilqr.Server(prm, hbm_budget_bytes=(1 << 30) if mix == "pair" else (16 << 30),
                         max_batch=max_batch, max_inflight=inflight, max_N=50, sqp_iters=1,
                         warps=warps, class_params=classes if mix != "pair" else None,
-                        large_cta_budget=large_cta_budget)
+                        large_cta_budget=large_cta_budget, split_min_robots=split_min_robots,
+                        split_max_batch=split_max_batch)
     # a client's ticks run one after another (each warm-starts the next), so
     # the full mix spreads the offered rate over more clients
     n_clients = 256 if mix == "pair" else 1024
@@ -1035,6 +1056,9 @@ def measure_serving(pdilqr, args, seconds: float, rate: float, max_batch: int, w
            "p50_ms": pct(lat, 50) / 1e3, "p99_ms": pct(lat, 99) / 1e3,
            "mean_batch": st["mean_batch"], "max_batch": max_batch, "warps": warps,
            "streams": inflight, "large_cta_budget": large_cta_budget}
+    if split_min_robots:
+        out["split_min_robots"] = split_min_robots
+        out["split_max_batch"] = split_max_batch
     if mix != "pair":
         out["by_robots"] = {str(r): {"requests": len(v), "p50_ms": pct(v, 50) / 1e3,
                                      "p99_ms": pct(v, 99) / 1e3}
@@ -1199,6 +1223,15 @@ def main():
                     help="large_cta_budget of the full-mix server: most instances of 4+ robots "
                          "in flight (0: no budget; with 8 streams a budget of 32 or 64 did not "
                          "bring the small classes back to their 4-stream latency)")
+    ap.add_argument("--mix-split-seconds", type=float, default=30.0,
+                    help="duration of the full mix with the large classes on the split scan "
+                         "(0 skips it)")
+    ap.add_argument("--mix-split-robots", type=int, default=16,
+                    help="split_min_robots of that server: classes of this many robots or more "
+                         "run the split scan (4, 8 or 16; 8 and 4 measured a higher overall p99)")
+    ap.add_argument("--mix-split-batch", type=int, default=8,
+                    help="split_max_batch of that server: most instances of one split batch "
+                         "(4 could not keep up with 200 sixteen-robot requests/s)")
     ap.add_argument("--mix-streams", type=int, default=4,
                     help="batches in flight (streams) of the full-mix server, 1..16 (8 measured "
                          "worse than 4: large-class batches then occupy every SM and the "
