@@ -401,8 +401,10 @@ typedef struct {
                                /* SQP iteration (as pdilqr_opts.split); at most  */
                                /* one split batch is in flight.  0: none (every  */
                                /* class runs the fused kernel)                   */
-    int32_t split_max_batch;   /* most instances of one split batch (0: 4; each   */
-                               /* holds 16 SMs while it runs)                    */
+    int32_t split_max_batch;   /* most instances of one split batch (0: 8; each   */
+                               /* holds 16 SMs while it runs); with split classes */
+                               /* 16 x split_max_batch above the device's SM     */
+                               /* count is an invalid argument                   */
 } pdilqr_serve_opts;
 
 typedef struct {

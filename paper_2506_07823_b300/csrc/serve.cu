@@ -640,7 +640,7 @@ extern "C" pdilqr_status pdilqr_serve_create(const pdilqr_serve_opts* o, pdilqr_
     if (sv->opts.max_N <= 0) sv->opts.max_N = 100;
     if (sv->opts.sqp_iters <= 0) sv->opts.sqp_iters = 1;
     if (sv->opts.warps == 0) sv->opts.warps = 8;
-    if (sv->opts.split_max_batch <= 0) sv->opts.split_max_batch = 4;
+    if (sv->opts.split_max_batch <= 0) sv->opts.split_max_batch = 8;
     const int smr = sv->opts.split_min_robots;
     if (smr != 0 && smr != 4 && smr != 8 && smr != 16) {
         delete sv;
@@ -655,6 +655,18 @@ extern "C" pdilqr_status pdilqr_serve_create(const pdilqr_serve_opts* o, pdilqr_
     if (cudaGetDevice(&sv->device) != cudaSuccess) {
         delete sv;
         return PDILQR_E_CUDA;
+    }
+    if (smr != 0) {
+        // a split batch's CTAs must all be resident at once (one SM each at least)
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device) != cudaSuccess) {
+            delete sv;
+            return PDILQR_E_CUDA;
+        }
+        if ((int64_t)sv->opts.split_max_batch * kSplitChunks > sms) {
+            delete sv;
+            return PDILQR_E_INVALID_ARG;
+        }
     }
     void* p = nullptr;
     if (cudaMalloc(&p, (size_t)sv->opts.hbm_budget_bytes) != cudaSuccess) {

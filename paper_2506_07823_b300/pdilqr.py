@@ -426,7 +426,8 @@ class Server:
         ``large_cta_budget``: most instances of 4+ robots in flight (0: none).
         ``split_min_robots``: classes of at least this many robots (4, 8, 16) run
         the split scan, 16 CTAs per instance, one such batch in flight (0: none);
-        ``split_max_batch``: most instances of one split batch (0: 4)."""
+        ``split_max_batch``: most instances of one split batch (0: 8; 16 per
+        instance may not exceed the SM count)."""
         cm = None
         if class_params is not None:
             cm = (SrbdModel * len(SERVE_NROB))(

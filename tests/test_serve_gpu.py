@@ -298,3 +298,8 @@ def test_split_classes_match_oracle():
     with pytest.raises(pdilqr.PdilqrError) as e:
         make_server(split_min_robots=3)
     assert e.value.code == pdilqr.E_INVALID_ARG
+    # 16 CTAs per instance: a batch cap whose CTAs cannot all be resident
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    with pytest.raises(pdilqr.PdilqrError) as e:
+        make_server(split_min_robots=16, split_max_batch=sms // 16 + 1)
+    assert e.value.code == pdilqr.E_INVALID_ARG
