@@ -232,12 +232,12 @@ def sample_size(cores: int) -> int:
 
 # ------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clock samples (every 200 ms) during the timed region.
+    """nvidia-smi clock samples (every 50 ms) during the timed region.
 
     ``start`` returns once nvidia-smi has printed its first sample (at most
     5 s), so that its start-up does not eat into the region; the summary keeps
-    the last sample taken before the region (the GPU busy with the warm-up
-    steps) and every sample taken inside it."""
+    the samples taken inside the region, or, when the region was shorter than
+    the interval, the last one before it (``samples_in_region`` says which)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -254,14 +254,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
             t0 = time.perf_counter()
             while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
                 time.sleep(0.01)
-            self._skip = max(0, len(self.lines) - 1)
+            self._skip = len(self.lines)
         except FileNotFoundError:
             self.proc = None
 
@@ -281,7 +281,8 @@ class ClockSampler:
             self._t.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines[self._skip:]:
+        inside = self.lines[self._skip:]
+        for ln in inside or self.lines[-1:]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -295,7 +296,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "samples_in_region": len(inside), "reasons": sorted(reasons)}
 
 
 # ------------------------------------------------------------- multi-rank
